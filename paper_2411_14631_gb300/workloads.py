@@ -1,0 +1,241 @@
+"""Seeded synthetic inputs shared by the CUDA path and the oracle.
+
+This module only generates inputs: oct lists ``(level, ix, iy, iz)`` (oct coordinates at
+the oct's level, 2^(level-1) octs per dimension) and primitive fields
+``W = (rho, u, v, w, p)`` sampled at cell centres.  It contains no step of the hydro
+scheme; each side converts primitives to conserved variables with its own code.
+
+Workloads (shapes of the paper's runs: clustered, multi-level, high density contrast,
+Sec. 1 and Sec. 3.1 of arXiv 2411.14631; the paper's cosmological and galaxy initial
+conditions are not available, these synthetic fields stand in for them):
+
+* ``sod``          -- 3D Sod tube, split at x = 0.5 (Toro 2009, Sec. 4.3.3, test 1).
+* ``turbulent``    -- periodic box, log-normal density from a Gaussian random field with
+                      P(k) ~ k^-4, Gaussian velocity field of rms Mach 2, p = rho.
+* ``plummer``      -- Plummer-like clumps (core 0.005, contrast 1e4) on a base level,
+                      refined by a quasi-Lagrangian mass threshold, 2:1 balanced.
+* ``sedov``        -- point blast, E = 1 deposited in one cell, rho = 1, p = 1e-5.
+* ``random_tree``  -- tiny random balanced octrees for table tests.
+"""
+import itertools
+
+import numpy as np
+
+PERIODIC, OUTFLOW = 0, 1
+
+
+def _pack(x, y, z):
+    return (x.astype(np.int64) << 42) | (y.astype(np.int64) << 21) | z.astype(np.int64)
+
+
+def _unpack(k):
+    m = (1 << 21) - 1
+    return (k >> 42) & m, (k >> 21) & m, k & m
+
+
+def full_level(level):
+    """All octs of one complete level, as packed coordinates."""
+    n = 1 << (level - 1)
+    g = np.arange(n, dtype=np.int64)
+    x, y, z = np.meshgrid(g, g, g, indexing="ij")
+    return np.unique(_pack(x.ravel(), y.ravel(), z.ravel()))
+
+
+def to_lxyz(levels):
+    """dict level -> packed coords  ->  (n, 4) int32 array of (level, ix, iy, iz)."""
+    out = []
+    for l in sorted(levels):
+        x, y, z = _unpack(levels[l])
+        out.append(np.stack([np.full(x.shape, l), x, y, z], axis=1))
+    return np.concatenate(out).astype(np.int32)
+
+
+def balance(levels, periodic=True):
+    """Add octs until every oct's father has all 26 father-level neighbours present
+    (the 2:1 rule of a fully threaded octree), finest level first."""
+    lmax = max(levels)
+    for l in range(lmax, 1, -1):
+        if l not in levels or levels[l].size == 0:
+            continue
+        x, y, z = _unpack(levels[l])
+        n = 1 << (l - 1)           # father-level cells per dimension
+        need = []
+        for dx, dy, dz in itertools.product((-1, 0, 1), repeat=3):
+            px, py, pz = x + dx, y + dy, z + dz
+            if periodic:
+                px, py, pz = px % n, py % n, pz % n
+                keep = slice(None)
+            else:
+                keep = (px >= 0) & (px < n) & (py >= 0) & (py < n) & (pz >= 0) & (pz < n)
+            need.append(_pack(px[keep] >> 1, py[keep] >> 1, pz[keep] >> 1))
+        levels[l - 1] = np.unique(np.concatenate([levels.get(l - 1, np.empty(0, np.int64))] + need))
+    return levels
+
+
+def uniform_tree(level):
+    """Complete octree down to ``level`` (levels 1..level all full)."""
+    return to_lxyz({l: full_level(l) for l in range(1, level + 1)})
+
+
+def random_tree(base, extra, seed, p_refine=0.3, periodic=True):
+    """Random balanced octree: complete to ``base``, then up to ``extra`` random levels."""
+    rng = np.random.default_rng(seed)
+    levels = {l: full_level(l) for l in range(1, base + 1)}
+    cur = levels[base]
+    for l in range(base + 1, base + extra + 1):
+        x, y, z = _unpack(cur)
+        kids = []
+        for c in range(8):
+            pick = rng.random(x.size) < p_refine
+            kids.append(_pack(2 * x[pick] + (c & 1), 2 * y[pick] + ((c >> 1) & 1), 2 * z[pick] + ((c >> 2) & 1)))
+        cur = np.unique(np.concatenate(kids))
+        if cur.size == 0:
+            break
+        levels[l] = cur
+    return to_lxyz(balance(levels, periodic))
+
+
+def cell_centres(lxyz):
+    """Cell centres (n*8, 3) for an oct list in the given order (cell = oct*8 + c)."""
+    l = lxyz[:, 0].astype(np.int64)
+    base = lxyz[:, 1:4].astype(np.float64) * 2
+    c = np.arange(8)
+    off = np.stack([c & 1, (c >> 1) & 1, (c >> 2) & 1], axis=1)
+    dx = np.ldexp(1.0, -l)
+    return ((base[:, None, :] + off[None] + 0.5) * dx[:, None, None]).reshape(-1, 3)
+
+
+# ---- primitive fields, W[var][cell] -------------------------------------------------
+def sod_prims(xyz, axis=0):
+    left = xyz[:, axis] < 0.5
+    W = np.zeros((5, xyz.shape[0]))
+    W[0] = np.where(left, 1.0, 0.125)
+    W[4] = np.where(left, 1.0, 0.1)
+    return W
+
+
+def uniform_prims(xyz, rho=1.0, vel=(0.0, 0.0, 0.0), p=1.0):
+    W = np.empty((5, xyz.shape[0]))
+    W[0] = rho
+    W[1:4] = np.asarray(vel, dtype=np.float64)[:, None]
+    W[4] = p
+    return W
+
+
+def grf(n, seed, slope=-4.0):
+    """Unit-variance Gaussian random field on an n^3 periodic grid with P(k) ~ k^slope
+    (integer wavenumbers, k = 0 removed): seeded white noise shaped in Fourier space."""
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal((n, n, n))
+    f = np.fft.rfftn(noise)
+    k1 = np.fft.fftfreq(n) * n
+    kz = np.fft.rfftfreq(n) * n
+    k2 = k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + kz[None, None, :] ** 2
+    amp = np.zeros_like(k2)
+    nz = k2 > 0
+    amp[nz] = k2[nz] ** (slope / 4.0)            # sqrt(P) = k^(slope/2)
+    d = np.fft.irfftn(f * amp, s=(n, n, n))
+    d -= d.mean()
+    return d / d.std()
+
+
+TURB_SEED = 241114631
+
+
+def turbulent_fields(level, seed=TURB_SEED, sigma=1.0, mach=2.0):
+    """Grid fields of the turbulent box: rho = exp(sigma*delta - sigma^2/2),
+    velocities from three more fields scaled to 3D rms |v| = mach (c_s = 1), p = rho."""
+    n = 1 << level
+    delta = grf(n, seed)
+    rho = np.exp(sigma * delta - 0.5 * sigma * sigma)
+    v = np.stack([grf(n, seed + k) for k in (1, 2, 3)])
+    v *= mach / np.sqrt(np.mean(np.sum(v * v, axis=0)))
+    return rho, v
+
+
+def grid_prims(xyz, level, rho, v, p=None):
+    """Sample grid fields (level-l cells) at cell centres of level >= l."""
+    n = 1 << level
+    idx = np.minimum((xyz * n).astype(np.int64), n - 1)
+    W = np.empty((5, xyz.shape[0]))
+    W[0] = rho[idx[:, 0], idx[:, 1], idx[:, 2]]
+    for d in range(3):
+        W[1 + d] = v[d][idx[:, 0], idx[:, 1], idx[:, 2]]
+    W[4] = W[0] if p is None else p[idx[:, 0], idx[:, 1], idx[:, 2]]
+    return W
+
+
+PLUMMER_A, PLUMMER_CONTRAST = 0.005, 1e4
+
+
+def plummer_centres(nclump=64, seed=3):
+    return np.random.default_rng(seed).random((nclump, 3))
+
+
+def plummer_density(xyz, centres, a=PLUMMER_A, contrast=PLUMMER_CONTRAST, chunk=1 << 20):
+    """rho = 1 + sum_clumps contrast * (1 + r^2/a^2)^(-5/2), periodic minimum image."""
+    out = np.ones(xyz.shape[0])
+    for s in range(0, xyz.shape[0], chunk):
+        x = xyz[s:s + chunk]
+        acc = np.zeros(x.shape[0])
+        for c in centres:
+            d = x - c
+            d -= np.round(d)
+            r2 = np.einsum("ij,ij->i", d, d)
+            acc += contrast * (1.0 + r2 / (a * a)) ** -2.5
+        out[s:s + chunk] += acc
+    return out
+
+
+def plummer_tree(base=7, lmax=12, nclump=64, seed=3):
+    """Base level complete; a level-l cell (base <= l < lmax) is refined iff
+    rho * dx_l^3 > dx_base^3 (a mass threshold of one background base cell, i.e.
+    rho > 8^(l-base)), strict; then 2:1 balanced (periodic)."""
+    centres = plummer_centres(nclump, seed)
+    levels = {l: full_level(l) for l in range(1, base + 1)}
+    cur = levels[base]
+    a, K = PLUMMER_A, PLUMMER_CONTRAST
+    for l in range(base, lmax):
+        thr = 8.0 ** (l - base)
+        x, y, z = _unpack(cur)
+        kids = []
+        for c in range(8):
+            cx, cy, cz = 2 * x + (c & 1), 2 * y + ((c >> 1) & 1), 2 * z + ((c >> 2) & 1)
+            if l > base:
+                # only cells where one clump alone could pass: other clumps add < 1
+                rcut2 = a * a * ((K / max(thr - 2.0, 1e-30)) ** 0.4 - 1.0)
+                xyz = (np.stack([cx, cy, cz], axis=1) + 0.5) * np.ldexp(1.0, -l)
+                d = xyz[:, None, :] - centres[None]
+                d -= np.round(d)
+                near = (np.einsum("ijk,ijk->ij", d, d) <= rcut2).any(axis=1)
+                cx, cy, cz = cx[near], cy[near], cz[near]
+            xyz = (np.stack([cx, cy, cz], axis=1) + 0.5) * np.ldexp(1.0, -l)
+            rho = plummer_density(xyz, centres)
+            pick = rho > thr
+            kids.append(_pack(cx[pick], cy[pick], cz[pick]))
+        cur = np.unique(np.concatenate(kids))
+        if cur.size == 0:
+            break
+        levels[l + 1] = cur
+    return to_lxyz(balance(levels, periodic=True)), centres
+
+
+def plummer_prims(xyz, centres):
+    W = np.zeros((5, xyz.shape[0]))
+    W[0] = plummer_density(xyz, centres)
+    W[4] = W[0]
+    return W
+
+
+def sedov_prims(xyz, level, e_blast=1.0, rho=1.0, p=1e-5, gamma=1.4):
+    """Uniform gas with the blast energy added, as pressure, to the cell whose lower
+    corner is the box centre (index n/2 on each axis)."""
+    n = 1 << level
+    W = uniform_prims(xyz, rho=rho, p=p)
+    idx = np.floor(xyz * n).astype(np.int64)
+    hit = np.all(idx == n // 2, axis=1) & np.all(np.abs(xyz * n - (idx + 0.5)) < 1e-9, axis=1)
+    W[4, hit] = p + (gamma - 1.0) * e_blast * n ** 3
+    return W
+
+
+SOD_GAMMA, TURB_GAMMA, PLUMMER_GAMMA, SEDOV_GAMMA = 1.4, 5.0 / 3.0, 5.0 / 3.0, 1.4

@@ -1,0 +1,176 @@
+/*
+ * amrhydro -- C ABI of the GB300 (sm_103a) AMR Godunov hydro hot path.
+ *
+ * The operations are those of RAMSES' level step as named in arXiv 2411.14631:
+ * Table 1 lists godunov_fine (the hydro solver), newdt_fine (time stepping) and
+ * refine_fine (refinement); Sec. 1 describes the fully threaded octree (cubic cells
+ * split recursively into eight octants) and the Peano-Hilbert ordering of space.  The
+ * paper prints no hydro scheme; the one computed here is the unsplit MUSCL-Hancock
+ * scheme (MinMod slopes, HLLC or exact Riemann solver) on the octree with one global
+ * time step for all levels (the "single time step" option discussed with Eq. 1,
+ * Sec. 2.3), refluxing at coarse-fine faces and restriction of refined cells.
+ *
+ * Conventions shared by every entry point:
+ *   - Level l has 2^l cells per dimension in the unit box; dx_l = 2^-l.  An oct at
+ *     level l holds 2^3 level-l cells and has oct coordinates (ix,iy,iz) in
+ *     [0, 2^(l-1)); its father cell is the level-(l-1) cell (ix,iy,iz).
+ *   - Octs are numbered by (level, Hilbert key); cell id = oct*8 + c with
+ *     c = cx + 2 cy + 4 cz.
+ *   - State arrays are FP64 structure-of-arrays u[v*ncell + cell], ncell = 8*noct,
+ *     v = rho, rho u, rho v, rho w, E (conserved) or rho, u, v, w, p (primitive).
+ *   - Every pointer named d_* is device memory owned by the caller; h_* is host memory.
+ *     The library never allocates device memory and never frees caller memory.
+ *   - Calls that take a stream are asynchronous on it, make no host synchronisation
+ *     and read the time step through a device pointer, so a sequence of them can be
+ *     captured in a CUDA graph.  amr_build_octree and amr_get_status synchronise.
+ *   - Argument errors are returned at once.  Errors found on the device (a
+ *     non-physical state, a failed exact solve) are written to params->d_status
+ *     (first error wins) and read with amr_get_status.  Nothing aborts or traps.
+ */
+#ifndef AMRHYDRO_H
+#define AMRHYDRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *amr_stream;   /* a cudaStream_t; NULL = the legacy default stream */
+
+typedef enum {
+    AMR_OK = 0,
+    AMR_EINVAL = -1,        /* bad argument or malformed oct list */
+    AMR_EUNBALANCED = -2,   /* an oct's father lacks a father-level neighbour (2:1 rule) */
+    AMR_ECAPACITY = -3,     /* a caller buffer is smaller than the query said */
+    AMR_ECUDA = -4,         /* a CUDA runtime call failed */
+    AMR_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
+    AMR_ENONPHYSICAL = -6,  /* vacuum in an exact Riemann problem (HLLC flux used instead) */
+    AMR_ENOCONV = -7        /* exact Riemann Newton iteration did not converge (HLLC used) */
+} amr_status;
+
+enum { AMR_BC_PERIODIC = 0, AMR_BC_OUTFLOW = 1 };
+enum { AMR_RIEMANN_HLLC = 0, AMR_RIEMANN_EXACT = 1, AMR_RIEMANN_MLP = 2 };
+enum { AMR_PREC_FP64 = 0, AMR_PREC_FP32 = 1 };
+
+#define AMR_MAXLEV 21
+#define AMR_NCOUNTERS 8
+
+/* Mesh description for amr_build_octree. */
+typedef struct {
+    int32_t levelmin;   /* levels 1..levelmin are complete; 2 <= levelmin */
+    int32_t bc[6];      /* box faces -x,+x,-y,+y,-z,+z: AMR_BC_PERIODIC (both faces of an axis) or AMR_BC_OUTFLOW */
+} amr_geom;
+
+/* Scheme parameters.  gamma: ratio of specific heats; cfl: Courant number of the
+   time step; rho_floor, p_floor: floors applied after cons->prim and to face states;
+   riemann: AMR_RIEMANN_*; precision: AMR_PREC_FP64 (all arithmetic in FP64) or
+   AMR_PREC_FP32 (reconstruction and Riemann solve in FP32, state accumulation in FP64);
+   tile: 1 or 2 = depth of the oct tiles a CTA updates (8 or 64 octs), 0 = default;
+   mlp_weights: device pointer to the surrogate's weights (AMR_RIEMANN_MLP only);
+   mlp_resid_tol: acceptance threshold of the surrogate's residual check;
+   d_status: device int32 error word (may be NULL); d_counters: device uint64
+   counters[AMR_NCOUNTERS] (may be NULL): [0] faces solved by the surrogate,
+   [1] surrogate fallbacks to the exact solver, [2] exact-solver failures. */
+typedef struct {
+    double gamma, cfl, rho_floor, p_floor;
+    int32_t riemann, precision, tile, reserved;
+    const void *mlp_weights;
+    float mlp_resid_tol, reserved_f;
+    int32_t *d_status;
+    unsigned long long *d_counters;
+} hydro_params;
+
+/* The octree: host metadata plus non-owning views into the caller's tree memory.
+   Filled by amr_build_octree; the caller keeps the tree memory alive while in use. */
+typedef struct {
+    int64_t noct;
+    int32_t levelmin, levelmax;
+    int32_t bc[6];
+    int64_t lvl_off[AMR_MAXLEV + 2];        /* octs of level l: [lvl_off[l], lvl_off[l+1]) */
+    int64_t tile_off[2][AMR_MAXLEV + 2];    /* tiles of depth d+1 updating level l */
+    int64_t reg_base;                       /* first oct owning a flux-register row */
+    int32_t *lvl, *ix, *iy, *iz;            /* per oct: level, oct coordinates */
+    uint64_t *key;                          /* per oct: Hilbert key, 3*(level-1) bits */
+    int32_t *son;                           /* per cell: child oct or -1 */
+    int32_t *father;                        /* per oct: father cell, -1 at level 1 */
+    int32_t *nbor;                          /* per oct x 6: father-level face-neighbour cell, -1 beyond an outflow face */
+    int32_t *nb27;                          /* per oct x 27: same-level neighbour oct, -(1+coarse cell), or INT32_MIN beyond an outflow face */
+    uint8_t *refmask;                       /* per oct: bit c set iff cell c is refined */
+    int32_t *tile_root[2];                  /* per tile: root oct (level l-d-1) */
+    int32_t *tile_slot[2];                  /* per tile: (2^(d+1)+2)^3 stencil slots */
+} amr_tree;
+
+/* Sizes of the caller buffers amr_build_octree needs for this oct list (host list of
+   n_oct records (level, ix, iy, iz), int32).  Pure host computation. */
+amr_status amr_build_octree_query(const amr_geom *geom, const int32_t *h_oct_lxyz, int64_t n_oct,
+                                  size_t *tree_bytes, size_t *workspace_bytes);
+
+/* Build the octree (Sec. 1: fully threaded tree; Peano-Hilbert order): copy the oct
+   list to the device, compute Hilbert keys, sort by (level, key), build son / father /
+   nbor / nb27 / refmask and the tile stencil tables, check levels 1..levelmin complete,
+   no duplicates, and the 2:1 rule.  d_tree_mem (tree_bytes, 256-byte aligned) holds the
+   result; d_workspace (workspace_bytes) is scratch.  Synchronises the stream. */
+amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oct_lxyz, int64_t n_oct,
+                            void *d_tree_mem, size_t tree_bytes, void *d_workspace, size_t workspace_bytes,
+                            amr_tree *out, amr_stream stream);
+
+/* Primitive -> conserved for every cell, then restriction of refined cells (mean of
+   their eight children), finest level first.  Sets a consistent initial state. */
+amr_status hydro_init_from_prim(const amr_tree *tree, const hydro_params *params, const double *d_w,
+                                double *d_u, amr_stream stream);
+
+/* Conserved -> primitive for every cell, with the floors of params. */
+amr_status hydro_prim_of_state(const amr_tree *tree, const hydro_params *params, const double *d_u,
+                               double *d_w, amr_stream stream);
+
+/* newdt_fine (Table 1): *d_dt = cfl * min over leaf cells of dx_l / sum_d (|u_d| + c),
+   c = sqrt(gamma p / rho).  FP64 for AMR_PREC_FP64; for AMR_PREC_FP32 it is evaluated
+   in FP32, rounded to an FP32 value and scaled by (1 - 2^-16) so that it never exceeds
+   the FP64 result. */
+amr_status hydro_courant(const amr_tree *tree, const hydro_params *params, const double *d_u,
+                         double *d_dt, amr_stream stream);
+
+/* godunov_fine (Table 1) for one level (level >= levelmin) or for every level in one
+   launch (level = -1): for every oct of the level(s), gather the ghosted stencil
+   (interpolating from the coarser level where a neighbour is absent), MUSCL-Hancock
+   predictor, Riemann solve at every face, conservative update into d_u_new (all cells
+   of the level's octs), and flux-register rows (d_flux_reg, hydro_flux_reg_bytes) for
+   oct sides that face a coarser leaf.  Faces whose other side is a refined cell carry
+   no flux here.  d_dt: device scalar time step (read, not written).  d_dt_next: if not
+   NULL, receives atomically min(*d_dt_next, cfl * dx / sum(|u_d|+c)) over the leaf
+   cells whose new value is final after this call (the CFL step of the next step, fused);
+   hydro_reflux_level adds the cells it corrects.  Initialise it to a large value. */
+amr_status hydro_godunov_level(const amr_tree *tree, int level, const hydro_params *params,
+                               const double *d_u_old, double *d_u_new, double *d_flux_reg,
+                               const double *d_dt, double *d_dt_next, amr_stream stream);
+
+size_t hydro_flux_reg_bytes(const amr_tree *tree);
+
+/* Refluxing and restriction for coarse level `level`, run from the finest level up
+   after every hydro_godunov_level of the step: each leaf cell of the level next to a
+   refined cell receives -/+ dt/dx * 1/4 * (sum of the four fine fluxes) from the flux
+   register; then each refined cell becomes the mean of its children.  d_dt_next as in
+   hydro_godunov_level, for the corrected cells. */
+amr_status hydro_reflux_level(const amr_tree *tree, int level, const hydro_params *params,
+                              const double *d_flux_reg, double *d_u_new, const double *d_dt,
+                              double *d_dt_next, amr_stream stream);
+
+/* One whole step: resets *d_dt_next (if not NULL) to a large value, then godunov on
+   every level (one launch), then reflux + restriction from the finest level up.
+   Equivalent to the calls above in that order. */
+amr_status hydro_step(const amr_tree *tree, const hydro_params *params, const double *d_u_old,
+                      double *d_u_new, double *d_flux_reg, const double *d_dt, double *d_dt_next,
+                      amr_stream stream);
+
+/* Copy params->d_status and params->d_counters to the host (synchronises the device). */
+amr_status amr_get_status(const hydro_params *params, int32_t *h_status, unsigned long long *h_counters);
+
+const char *amr_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -73,6 +73,7 @@ def lib():
         L.or_oct_stencil.argtypes = [P, P, C.c_int64, P]
         L.or_courant.argtypes = [P, P, P, P]
         L.or_level_update.argtypes = [P, P, C.c_int, P, P, P, C.c_double]
+        L.or_octs_update.argtypes = [P, P, C.c_int64, C.c_int64, P, P, P, C.c_double]
         L.or_reflux_restrict.argtypes = [P, P, C.c_int, P, P, C.c_double]
         L.or_step.argtypes = [P, P, P, P, P, C.c_int]
         L.or_init_from_prim.argtypes = [P, P, P, P]

@@ -260,6 +260,27 @@ int or_level_update(const or_tree *t, const or_params *p, int level, const doubl
     return st;
 }
 
+/* the Godunov update of octs [o0, o1) only (same arithmetic as or_level_update) */
+int or_octs_update(const or_tree *t, const or_params *p, int64_t o0, int64_t o1, const double *u_old, double *u_new,
+                   double *reg, double dt)
+{
+    int st = OR_OK;
+    #pragma omp parallel
+    {
+        oct_work *wk = malloc(sizeof(oct_work));
+        int lst = OR_OK;
+        #pragma omp for schedule(static)
+        for (int64_t o = o0; o < o1; o++) {
+            int r = oct_update(t, p, o, u_old, u_new, reg, dt, wk);
+            if (r != OR_OK && lst == OR_OK) lst = r;
+        }
+        #pragma omp critical
+        { if (lst != OR_OK && st == OR_OK) st = lst; }
+        free(wk);
+    }
+    return st;
+}
+
 int or_reflux_restrict(const or_tree *t, const or_params *p, int level, const double *reg, double *u_new, double dt)
 {
     (void)p;

@@ -77,6 +77,8 @@ int or_oct_stencil(const or_tree *t, const double *u, int64_t oct, double *stenc
 int or_courant(const or_tree *t, const or_params *p, const double *u, double *dt);
 int or_level_update(const or_tree *t, const or_params *p, int level, const double *u_old, double *u_new,
                     double *reg /*[noct][6][5]*/, double dt);
+int or_octs_update(const or_tree *t, const or_params *p, int64_t o0, int64_t o1, const double *u_old, double *u_new,
+                   double *reg, double dt);
 int or_reflux_restrict(const or_tree *t, const or_params *p, int level, const double *reg, double *u_new, double dt);
 int or_step(const or_tree *t, const or_params *p, const double *u_old, double *u_new, double *dt_out, int nthreads);
 int or_init_from_prim(const or_tree *t, const or_params *p, const double *w, double *u);

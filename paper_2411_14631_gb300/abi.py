@@ -1,0 +1,87 @@
+"""ctypes view of include/amrhydro.h and loader of the in-tree libamrhydro.so.
+
+Argument marshalling only: every computation runs in the library's CUDA kernels.
+Loading fails loudly if the library is missing; there is no other implementation."""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libamrhydro.so")
+MAXLEV = 21
+NCOUNTERS = 8
+
+OK, EINVAL, EUNBALANCED, ECAPACITY, ECUDA, ETIMEOUT, ENONPHYSICAL, ENOCONV = 0, -1, -2, -3, -4, -5, -6, -7
+BC_PERIODIC, BC_OUTFLOW = 0, 1
+RIEMANN_HLLC, RIEMANN_EXACT, RIEMANN_MLP = 0, 1, 2
+PREC_FP64, PREC_FP32 = 0, 1
+
+EXPORTS = ["amr_build_octree_query", "amr_build_octree", "hydro_init_from_prim", "hydro_prim_of_state",
+           "hydro_courant", "hydro_godunov_level", "hydro_flux_reg_bytes", "hydro_reflux_level", "hydro_step",
+           "amr_get_status", "amr_status_string"]
+
+
+class AmrGeom(C.Structure):
+    _fields_ = [("levelmin", C.c_int32), ("bc", C.c_int32 * 6)]
+
+
+class HydroParams(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("rho_floor", C.c_double), ("p_floor", C.c_double),
+                ("riemann", C.c_int32), ("precision", C.c_int32), ("tile", C.c_int32), ("reserved", C.c_int32),
+                ("mlp_weights", C.c_void_p), ("mlp_resid_tol", C.c_float), ("reserved_f", C.c_float),
+                ("d_status", C.c_void_p), ("d_counters", C.c_void_p)]
+
+
+class AmrTree(C.Structure):
+    _fields_ = [("noct", C.c_int64), ("levelmin", C.c_int32), ("levelmax", C.c_int32), ("bc", C.c_int32 * 6),
+                ("lvl_off", C.c_int64 * (MAXLEV + 2)), ("tile_off", (C.c_int64 * (MAXLEV + 2)) * 2),
+                ("reg_base", C.c_int64),
+                ("lvl", C.c_void_p), ("ix", C.c_void_p), ("iy", C.c_void_p), ("iz", C.c_void_p),
+                ("key", C.c_void_p), ("son", C.c_void_p), ("father", C.c_void_p), ("nbor", C.c_void_p),
+                ("nb27", C.c_void_p), ("refmask", C.c_void_p), ("tile_root", C.c_void_p * 2),
+                ("tile_slot", C.c_void_p * 2)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libamrhydro.so (built by ``paper_2411_14631_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libamrhydro.so is not built (run paper_2411_14631_gb300.build.build()); "
+                           "the hydro path has no other implementation")
+    L = C.CDLL(LIB_PATH)
+    P, S = C.c_void_p, C.c_size_t
+    PT, PP = C.POINTER(AmrTree), C.POINTER(HydroParams)
+    L.amr_build_octree_query.argtypes = [C.POINTER(AmrGeom), P, C.c_int64, C.POINTER(S), C.POINTER(S)]
+    L.amr_build_octree.argtypes = [C.POINTER(AmrGeom), P, C.c_int64, P, S, P, S, PT, P]
+    L.hydro_init_from_prim.argtypes = [PT, PP, P, P, P]
+    L.hydro_prim_of_state.argtypes = [PT, PP, P, P, P]
+    L.hydro_courant.argtypes = [PT, PP, P, P, P]
+    L.hydro_godunov_level.argtypes = [PT, C.c_int, PP, P, P, P, P, P, P]
+    L.hydro_flux_reg_bytes.argtypes = [PT]
+    L.hydro_flux_reg_bytes.restype = S
+    L.hydro_reflux_level.argtypes = [PT, C.c_int, PP, P, P, P, P, P]
+    L.hydro_step.argtypes = [PT, PP, P, P, P, P, P, P]
+    L.amr_get_status.argtypes = [PP, P, P]
+    L.amr_status_string.argtypes = [C.c_int]
+    L.amr_status_string.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("hydro_flux_reg_bytes", "amr_status_string"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+class AmrError(RuntimeError):
+    def __init__(self, call, status):
+        self.status = status
+        msg = lib().amr_status_string(status).decode()
+        super().__init__("%s failed: %s (%d)" % (call, msg, status))
+
+
+def check(call, status):
+    if status != OK:
+        raise AmrError(call, status)

@@ -1,0 +1,406 @@
+// godunov_fine (Table 1 of arXiv 2411.14631) on GB300: one CTA updates one tile of
+// sibling octs.  A depth-D tile is the 2^D x 2^D x 2^D block of level-l octs below one
+// level-(l-D) oct; its ghosted stencil is (2^D+2)^3 oct slots = (2^(D+1)+4)^3 cells.
+// Phases, all through shared memory:
+//   1 gather the stencil from u_old (FP64 loads; a slot is a level-l oct, a coarse leaf
+//     cell interpolated to its eight children, a clamped outflow ghost, or unused),
+//     convert to primitives in the working precision R;
+//   2 MinMod slopes and the MUSCL-Hancock half-step predictor for every stencil cell
+//     that borders an updated cell;
+//   3 one Riemann solve per face touching an updated cell;
+//   4 FP64 conservative update of the tile's existing octs, fused CFL candidate for the
+//     next step, and flux-register rows for oct sides facing coarser leaves.
+#include <cfloat>
+#include "hydro_math.cuh"
+
+namespace amr {
+
+constexpr int32_t UNNEEDED_SLOT = INT32_MIN + 1;
+
+template <int D> struct Geo {
+    static constexpr int NS = (1 << D) + 2;      // slots per axis
+    static constexpr int NSLOT = NS * NS * NS;
+    static constexpr int C = 2 * NS;             // stencil cells per axis
+    static constexpr int NC = C * C * C;
+    static constexpr int P = C - 2;              // predicted cells per axis (stencil 1..C-2)
+    static constexpr int NP = P * P * P;
+    static constexpr int CI = 1 << (D + 1);      // updated cells per axis (stencil 2..C-3)
+    static constexpr int NI = CI * CI * CI;
+    static constexpr int NF = (CI + 1) * CI * CI;  // faces per direction
+    static constexpr int OI = 1 << D;            // interior oct slots per axis
+};
+
+struct GArgs {
+    TreeView tv;
+    const int32_t *tile_root, *tile_slot;
+    int64_t tile_off[AMR_MAXLEV + 2];
+    int64_t t_begin, t_end;
+    int32_t lfirst, llast;                 // levels covered by [t_begin, t_end)
+    const double *u_old;
+    double *u_new, *reg;
+    const double *dt;
+    double *dt_next;
+    double gamma, rho_floor, p_floor, cfl;
+    int32_t *status;
+    unsigned long long *counters;
+};
+
+// value of a neighbour of coarse leaf cell F (level lc, coordinates X) along axis d,
+// side s = +-1: the level-lc cell there, or the coarser leaf containing it
+__device__ __forceinline__ int64_t coarse_neighbour(const TreeView &tv, int64_t oF, const int64_t X[3], int lc,
+                                                    int d, int s)
+{
+    int64_t P[3] = {X[0], X[1], X[2]};
+    P[d] += s;
+    const int64_t n = int64_t(1) << lc;
+    if (P[d] < 0 || P[d] >= n) {
+        if (tv.bc[2 * d + (s > 0)] == AMR_BC_PERIODIC) P[d] = (P[d] + n) % n;
+        else P[d] = X[d];                       // outflow: clamp at the cell's own level
+    }
+    const int cc = int(P[0] & 1) + 2 * int(P[1] & 1) + 4 * int(P[2] & 1);
+    if ((P[0] >> 1) == tv.ix[oF] && (P[1] >> 1) == tv.iy[oF] && (P[2] >> 1) == tv.iz[oF]) return oF * 8 + cc;
+    const int32_t N = tv.nbor[6 * oF + 2 * d + (s > 0)];   // father-level neighbour of oF
+    if (N < 0) return oF * 8 + (int(X[0] & 1) + 2 * int(X[1] & 1) + 4 * int(X[2] & 1));              // unreachable for a valid tree; stay in bounds
+    const int32_t so = tv.son[N];
+    return so >= 0 ? int64_t(so) * 8 + cc : int64_t(N);
+}
+
+// child c of coarse leaf cell F: U_F + sum_d s_d/4 minmod(U_F - U_{F-e_d}, U_{F+e_d} - U_F)
+__device__ void interp_child(const TreeView &tv, const double *__restrict__ u, int64_t F, int c, double out[NV])
+{
+    const int64_t oF = F >> 3;
+    const int cf = int(F & 7);
+    const int lc = tv.lvl[oF];
+    const int64_t X[3] = {2 * int64_t(tv.ix[oF]) + (cf & 1), 2 * int64_t(tv.iy[oF]) + ((cf >> 1) & 1),
+                          2 * int64_t(tv.iz[oF]) + ((cf >> 2) & 1)};
+    int64_t nm[3], np[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        nm[d] = coarse_neighbour(tv, oF, X, lc, d, -1);
+        np[d] = coarse_neighbour(tv, oF, X, lc, d, +1);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double uc = u[v * tv.ncell + F];
+        double r = uc;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double m = minmod(uc - u[v * tv.ncell + nm[d]], u[v * tv.ncell + np[d]] - uc);
+            r = r + (((c >> d) & 1) ? 0.25 * m : -0.25 * m);
+        }
+        out[v] = r;
+    }
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return __double_as_longlong(x); }
+
+template <typename R, int D, int RS>
+struct Smem {
+    using G = Geo<D>;
+    R W[NV][G::NC];                 // stencil primitives; later reused for fluxes
+    R Q[4 * NV][G::NP];             // predicted state (5) + slopes (3 x 5)
+    int32_t slot[G::NSLOT];
+    uint8_t ref[G::NSLOT];
+    double dtmin[32];
+};
+
+template <typename R, int D, int RS>
+__global__ void __launch_bounds__(128) k_godunov(GArgs a)
+{
+    using G = Geo<D>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<R, D, RS> &sm = *reinterpret_cast<Smem<R, D, RS> *>(smem_raw);
+    R(*sF)[NV][G::NF] = reinterpret_cast<R(*)[NV][G::NF]>(&sm.W[0][0]);   // aliases W after phase 2
+    static_assert(3 * NV * G::NF <= NV * G::NC, "flux buffer must fit in the stencil buffer");
+    const TreeView &tv = a.tv;
+    const int tid = threadIdx.x;
+    const double dt = *a.dt;
+    Prm<R> pr;
+    pr.gamma = R(a.gamma); pr.rho_floor = R(a.rho_floor); pr.p_floor = R(a.p_floor);
+
+    for (int64_t t = a.t_begin + blockIdx.x; t < a.t_end; t += gridDim.x) {
+        // ---- level of this tile and its geometry
+        int l = a.lfirst;
+        while (l < a.llast && t >= a.tile_off[l + 1]) ++l;
+        const int32_t root = a.tile_root[t];
+        const int64_t n = int64_t(1) << l;                      // cells per dimension at level l
+        // a depth-D root covers 2^(D+1) level-l cells per axis; stencil index 0 is two cells before
+        const int64_t X0[3] = {int64_t(tv.ix[root]) * (2 << D) - 2, int64_t(tv.iy[root]) * (2 << D) - 2,
+                               int64_t(tv.iz[root]) * (2 << D) - 2};
+        const double dx = ldexp(1.0, -l);
+        const double lam = dt / dx;
+        int mine_out = 0;
+        for (int s = tid; s < G::NSLOT; s += blockDim.x) {
+            const int32_t e = a.tile_slot[t * G::NSLOT + s];
+            sm.slot[s] = e;
+            sm.ref[s] = e >= 0 ? tv.refmask[e] : 0;
+            mine_out |= (e == OUTSIDE);
+        }
+        const int any_outside = __syncthreads_or(mine_out);   // barrier: slots visible to all
+
+        // ---- phase 1: gather + primitives (c fastest so a warp reads whole octs)
+        for (int q = tid; q < G::NC; q += blockDim.x) {
+            const int s = q >> 3, c = q & 7;
+            const int sx = s % G::NS, sy = (s / G::NS) % G::NS, sz = s / (G::NS * G::NS);
+            const int i = 2 * sx + (c & 1), j = 2 * sy + ((c >> 1) & 1), k = 2 * sz + ((c >> 2) & 1);
+            const int si = i + G::C * (j + G::C * k);
+            const int32_t e = sm.slot[s];
+            if (e == OUTSIDE) continue;
+            double U[NV];
+            if (e >= 0) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) U[v] = a.u_old[v * tv.ncell + int64_t(e) * 8 + c];
+            } else if (e == UNNEEDED_SLOT) {
+                U[0] = 1.0; U[1] = 0.0; U[2] = 0.0; U[3] = 0.0; U[4] = 1.0;
+            } else {
+                interp_child(tv, a.u_old, int64_t(-1) - e, c, U);
+            }
+            R Wc[NV];
+            cons_to_prim(U, pr, Wc);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sm.W[v][si] = Wc[v];
+        }
+        __syncthreads();
+        if (any_outside) {
+            // outflow ghosts: copy the cell at the clamped coordinates (zero gradient)
+            for (int q = tid; q < G::NC; q += blockDim.x) {
+                const int i = q % G::C, j = (q / G::C) % G::C, k = q / (G::C * G::C);
+                int64_t g[3] = {X0[0] + i, X0[1] + j, X0[2] + k};
+                bool out = false;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (g[d] < 0) { g[d] = 0; out = true; }
+                    else if (g[d] >= n) { g[d] = n - 1; out = true; }
+                }
+                if (!out) continue;
+                const int src = int(g[0] - X0[0]) + G::C * (int(g[1] - X0[1]) + G::C * int(g[2] - X0[2]));
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sm.W[v][q] = sm.W[v][src];
+            }
+            __syncthreads();
+        }
+
+        // ---- phase 2: slopes + predictor on stencil cells 1..C-2
+        const R hl = R(0.5 * lam);
+        for (int p = tid; p < G::NP; p += blockDim.x) {
+            const int i = 1 + p % G::P, j = 1 + (p / G::P) % G::P, k = 1 + p / (G::P * G::P);
+            const int si = i + G::C * (j + G::C * k);
+            const int st[3] = {1, G::C, G::C * G::C};
+            R Wc[NV], Dl[3][NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Wc[v] = sm.W[v][si];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+                    Dl[d][v] = minmod(Wc[v] - sm.W[v][si - st[d]], sm.W[v][si + st[d]] - Wc[v]);
+            const R r = Wc[0], u = Wc[1], vv = Wc[2], w = Wc[3], pp = Wc[4];
+            R Wt[NV];
+            Wt[0] = r - hl * (u * Dl[0][0] + r * Dl[0][1] + vv * Dl[1][0] + r * Dl[1][2] + w * Dl[2][0] + r * Dl[2][3]);
+            Wt[1] = u - hl * (u * Dl[0][1] + vv * Dl[1][1] + w * Dl[2][1] + Dl[0][4] / r);
+            Wt[2] = vv - hl * (u * Dl[0][2] + vv * Dl[1][2] + w * Dl[2][2] + Dl[1][4] / r);
+            Wt[3] = w - hl * (u * Dl[0][3] + vv * Dl[1][3] + w * Dl[2][3] + Dl[2][4] / r);
+            Wt[4] = pp - hl * (u * Dl[0][4] + vv * Dl[1][4] + w * Dl[2][4] + pr.gamma * pp * (Dl[0][1] + Dl[1][2] + Dl[2][3]));
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sm.Q[v][p] = Wt[v];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sm.Q[NV + NV * d + v][p] = Dl[d][v];
+        }
+        __syncthreads();
+
+        // ---- phase 3: Riemann problem at every face touching an updated cell
+        for (int f = tid; f < 3 * G::NF; f += blockDim.x) {
+            const int d = f / G::NF, r0 = f % G::NF;
+            const int fa = r0 % (G::CI + 1), t1 = (r0 / (G::CI + 1)) % G::CI, t2 = r0 / ((G::CI + 1) * G::CI);
+            // predicted-cell coordinates (stencil - 1) of the left cell
+            int L[3];
+            if (d == 0) { L[0] = fa; L[1] = 1 + t1; L[2] = 1 + t2; }
+            else if (d == 1) { L[0] = 1 + t1; L[1] = fa; L[2] = 1 + t2; }
+            else { L[0] = 1 + t1; L[1] = 1 + t2; L[2] = fa; }
+            const int pl = L[0] + G::P * (L[1] + G::P * L[2]);
+            const int pR = pl + (d == 0 ? 1 : d == 1 ? G::P : G::P * G::P);
+            const int perm[3] = {d + 1, d == 0 ? 2 : 1, d == 2 ? 2 : 3};
+            R WL[NV], WR[NV];
+            WL[0] = sm.Q[0][pl] + R(0.5) * sm.Q[NV + NV * d][pl];
+            WR[0] = sm.Q[0][pR] - R(0.5) * sm.Q[NV + NV * d][pR];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                WL[1 + q] = sm.Q[perm[q]][pl] + R(0.5) * sm.Q[NV + NV * d + perm[q]][pl];
+                WR[1 + q] = sm.Q[perm[q]][pR] - R(0.5) * sm.Q[NV + NV * d + perm[q]][pR];
+            }
+            WL[4] = sm.Q[4][pl] + R(0.5) * sm.Q[NV + NV * d + 4][pl];
+            WR[4] = sm.Q[4][pR] - R(0.5) * sm.Q[NV + NV * d + 4][pR];
+            WL[0] = rmax(WL[0], pr.rho_floor); WR[0] = rmax(WR[0], pr.rho_floor);
+            WL[4] = rmax(WL[4], pr.p_floor); WR[4] = rmax(WR[4], pr.p_floor);
+            R Fn[NV];
+            if (RS == AMR_RIEMANN_EXACT) {
+                R ps, us;
+                const R tol = sizeof(R) == 8 ? R(1e-14) : R(1e-6);
+                const int e = exact_star(WL, WR, pr.gamma, tol, 50, ps, us);
+                if (e == 0) {
+                    R W0[NV], U0[NV];
+                    exact_sample0(WL, WR, pr.gamma, ps, us, W0);
+                    flux_normal(W0, pr.gamma, Fn, U0);
+                } else {
+                    set_error(a.status, e);
+                    hllc(WL, WR, pr.gamma, Fn);
+                }
+            } else {
+                hllc(WL, WR, pr.gamma, Fn);
+            }
+            sF[d][0][r0] = Fn[0];
+            sF[d][4][r0] = Fn[4];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sF[d][perm[q]][r0] = Fn[1 + q];
+        }
+        __syncthreads();
+
+        // ---- phase 4: FP64 update of existing cells + fused CFL candidate
+        double my_dt = DBL_MAX;
+        for (int q = tid; q < G::NI; q += blockDim.x) {
+            const int c = q & 7, o = q >> 3;
+            const int ox = 1 + o % G::OI, oy = 1 + (o / G::OI) % G::OI, oz = 1 + o / (G::OI * G::OI);
+            const int s = ox + G::NS * (oy + G::NS * oz);
+            const int32_t e = sm.slot[s];
+            if (e < 0) continue;                                    // no oct here: nothing to update
+            const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+            const int ii[3] = {2 * ox + cx - 2, 2 * oy + cy - 2, 2 * oz + cz - 2};   // interior coords 0..CI-1
+            double dU[NV] = {0, 0, 0, 0, 0};
+            bool nbref = false;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int t1 = ii[d == 0 ? 1 : 0], t2 = ii[d == 2 ? 1 : 2];
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    // neighbour cell across the face: stencil coords of this cell +- e_d
+                    int nc[3] = {ii[0] + 2, ii[1] + 2, ii[2] + 2};
+                    nc[d] += side ? 1 : -1;
+                    const int ns = (nc[0] >> 1) + G::NS * ((nc[1] >> 1) + G::NS * (nc[2] >> 1));
+                    const int ncc = (nc[0] & 1) + 2 * (nc[1] & 1) + 4 * (nc[2] & 1);
+                    if (sm.slot[ns] >= 0 && ((sm.ref[ns] >> ncc) & 1)) { nbref = true; continue; }
+                    const int fa = ii[d] + side;
+                    const int r0 = fa + (G::CI + 1) * (t1 + G::CI * t2);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const double F = double(sF[d][v][r0]);
+                        dU[v] = side ? dU[v] - F : dU[v] + F;
+                    }
+                }
+            }
+            const int64_t cell = int64_t(e) * 8 + c;
+            double Un[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                Un[v] = a.u_old[v * tv.ncell + cell] + lam * dU[v];
+                a.u_new[v * tv.ncell + cell] = Un[v];
+            }
+            if (a.dt_next && !nbref && !((sm.ref[s] >> c) & 1)) {
+                // CFL candidate (newdt_fine) from the final new state of this leaf cell
+                Prm<double> pd;
+                pd.gamma = a.gamma; pd.rho_floor = a.rho_floor; pd.p_floor = a.p_floor;
+                double Wn[NV];
+                cons_to_prim(Un, pd, Wn);
+                const double cs = sqrt(a.gamma * Wn[4] / Wn[0]);
+                const double sig = (fabs(Wn[1]) + cs) + (fabs(Wn[2]) + cs) + (fabs(Wn[3]) + cs);
+                const double cand = a.cfl * (dx / sig);
+                my_dt = cand < my_dt ? cand : my_dt;
+            }
+        }
+        if (a.dt_next) {
+            for (int off = 16; off > 0; off >>= 1) {
+                const double o = __shfl_xor_sync(0xffffffffu, my_dt, off);
+                my_dt = o < my_dt ? o : my_dt;
+            }
+            if ((tid & 31) == 0 && my_dt < DBL_MAX)
+                atomicMin(reinterpret_cast<unsigned long long *>(a.dt_next), dbits(my_dt));
+        }
+
+        // ---- flux register: oct sides whose neighbour slot is a coarse leaf
+        if (a.reg) {
+            for (int w = tid; w < G::OI * G::OI * G::OI * 6; w += blockDim.x) {
+                const int o = w / 6, f = w % 6, d = f >> 1, side = f & 1;
+                const int ox = 1 + o % G::OI, oy = 1 + (o / G::OI) % G::OI, oz = 1 + o / (G::OI * G::OI);
+                const int32_t e = sm.slot[ox + G::NS * (oy + G::NS * oz)];
+                if (e < 0 || e < tv.reg_base) continue;   // base-level octs never face a coarser leaf
+                int nsl[3] = {ox, oy, oz};
+                nsl[d] += side ? 1 : -1;
+                const int32_t en = sm.slot[nsl[0] + G::NS * (nsl[1] + G::NS * nsl[2])];
+                if (en >= 0 || en == OUTSIDE || en == UNNEEDED_SLOT) continue;
+                double sum[NV] = {0, 0, 0, 0, 0};
+                for (int c = 0; c < 8; ++c) {
+                    const int pc[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+                    if (pc[d] != side) continue;
+                    const int ii[3] = {2 * ox + pc[0] - 2, 2 * oy + pc[1] - 2, 2 * oz + pc[2] - 2};
+                    const int t1 = ii[d == 0 ? 1 : 0], t2 = ii[d == 2 ? 1 : 2];
+                    const int r0 = (ii[d] + side) + (G::CI + 1) * (t1 + G::CI * t2);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) sum[v] += double(sF[d][v][r0]);
+                }
+                const int64_t row = (int64_t(e) - tv.reg_base) * 6 + f;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) a.reg[row * NV + v] = sum[v];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename R, int D, int RS>
+static amr_status launch(const GArgs &a, int64_t ntile, cudaStream_t st)
+{
+    if (ntile <= 0) return AMR_OK;
+    const size_t bytes = sizeof(Smem<R, D, RS>);
+    auto kern = k_godunov<R, D, RS>;
+    AMR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+    const int64_t grid = ntile < 1048576 ? ntile : 1048576;
+    kern<<<unsigned(grid), 128, bytes, st>>>(a);
+    AMR_CUDA_TRY(cudaGetLastError());
+    return AMR_OK;
+}
+
+amr_status godunov_dispatch(const amr_tree *t, int level, const hydro_params *p, const double *u_old,
+                            double *u_new, double *reg, const double *dt, double *dt_next, cudaStream_t st)
+{
+    int depth = p->tile == 0 ? 1 : p->tile;
+    if (depth != 1 && depth != 2) return AMR_EINVAL;
+    if (depth == 2 && p->precision == AMR_PREC_FP64) return AMR_EINVAL;   // FP64 stencil of 12^3 cells exceeds smem
+    const int l0 = level < 0 ? t->levelmin : level, l1 = level < 0 ? t->levelmax : level;
+    if (l0 < t->levelmin || l1 > t->levelmax) return AMR_EINVAL;
+    // levels that cannot form tiles of this depth (root above level 1) use depth 1
+    int lsplit = l0;
+    while (lsplit <= l1 && lsplit - depth < 1) ++lsplit;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int d = pass == 0 ? 1 : depth;
+        const int la = pass == 0 ? l0 : lsplit, lb = pass == 0 ? lsplit - 1 : l1;
+        if (pass == 0 && depth == 1) continue;
+        if (la > lb) continue;
+        GArgs a;
+        a.tv = make_view(t);
+        a.tile_root = t->tile_root[d - 1];
+        a.tile_slot = t->tile_slot[d - 1];
+        for (int i = 0; i < AMR_MAXLEV + 2; ++i) a.tile_off[i] = t->tile_off[d - 1][i];
+        a.lfirst = la;
+        a.llast = lb;
+        a.t_begin = t->tile_off[d - 1][la];
+        a.t_end = t->tile_off[d - 1][lb + 1];
+        a.u_old = u_old; a.u_new = u_new; a.reg = reg; a.dt = dt; a.dt_next = dt_next;
+        a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
+        a.status = p->d_status; a.counters = p->d_counters;
+        const int64_t nt = a.t_end - a.t_begin;
+        amr_status r = AMR_OK;
+        const bool fp32 = p->precision == AMR_PREC_FP32;
+        const bool ex = p->riemann == AMR_RIEMANN_EXACT;
+        if (d == 1) {
+            if (fp32) r = ex ? launch<float, 1, 1>(a, nt, st) : launch<float, 1, 0>(a, nt, st);
+            else r = ex ? launch<double, 1, 1>(a, nt, st) : launch<double, 1, 0>(a, nt, st);
+        } else {
+            r = ex ? launch<float, 2, 1>(a, nt, st) : launch<float, 2, 0>(a, nt, st);
+        }
+        if (r != AMR_OK) return r;
+    }
+    return AMR_OK;
+}
+
+}  // namespace amr

@@ -1,0 +1,187 @@
+// Per-state arithmetic of the MUSCL-Hancock / Godunov scheme (device side), templated
+// on the working precision R (double for the FP64 path, float for the FP32 path).
+// The scheme: Toro 2009 -- MinMod slopes (Sec. 13.7), MUSCL-Hancock predictor in
+// primitive variables (Sec. 14.4), HLLC (Sec. 10.4, Davis wave speeds), exact Riemann
+// solver (Ch. 4: pressure function, Newton from the PVRS guess, sampling at x/t = 0).
+#pragma once
+#include "common.cuh"
+
+namespace amr {
+
+template <typename R> struct Prm {
+    R gamma, rho_floor, p_floor;
+};
+
+template <typename R> __device__ __forceinline__ R minmod(R a, R b)
+{
+    if (a * b <= R(0)) return R(0);
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+
+// conserved (FP64 storage) -> primitive in precision R, floors applied
+template <typename R>
+__device__ __forceinline__ void cons_to_prim(const double U[NV], const Prm<R> &p, R W[NV])
+{
+    const R rho = rmax(R(U[0]), p.rho_floor);
+    const R u = R(U[1]) / rho, v = R(U[2]) / rho, w = R(U[3]) / rho;
+    const R ek = R(0.5) * rho * (u * u + v * v + w * w);
+    const R pr = (p.gamma - R(1)) * (R(U[4]) - ek);
+    W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
+    W[4] = rmax(pr, p.p_floor);
+}
+
+// physical flux through a face whose normal is the first velocity component
+template <typename R>
+__device__ __forceinline__ void flux_normal(const R W[NV], R g, R F[NV], R U[NV])
+{
+    const R rho = W[0], u = W[1], v = W[2], w = W[3], pr = W[4];
+    const R E = pr / (g - R(1)) + R(0.5) * rho * (u * u + v * v + w * w);
+    F[0] = rho * u;
+    F[1] = rho * u * u + pr;
+    F[2] = rho * u * v;
+    F[3] = rho * u * w;
+    F[4] = u * (E + pr);
+    U[0] = rho; U[1] = rho * u; U[2] = rho * v; U[3] = rho * w; U[4] = E;
+}
+
+// HLLC flux (Toro, Spruce & Speares 1994); the side used is chosen before computing,
+// so every face does one star state (no divergent branches).
+template <typename R>
+__device__ __forceinline__ void hllc(const R WL[NV], const R WR[NV], R g, R F[NV])
+{
+    const R rL = WL[0], uL = WL[1], pL = WL[4];
+    const R rR = WR[0], uR = WR[1], pR = WR[4];
+    const R cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+    const R SL = fmin(uL - cL, uR - cR);
+    const R SR = fmax(uL + cL, uR + cR);
+    const R Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR));
+    const bool left = (SL >= R(0)) || (Ss >= R(0));
+    const bool star = !(SL >= R(0)) && (Ss >= R(0) || SR > R(0));
+    const R *WK = left ? WL : WR;
+    const R SK = left ? SL : SR;
+    R FK[NV], UK[NV];
+    flux_normal(WK, g, FK, UK);
+    if (star) {
+        const R rK = WK[0], uK = WK[1], pK = WK[4];
+        const R f = rK * (SK - uK) / (SK - Ss);
+        const R Us[NV] = {f, f * Ss, f * WK[2], f * WK[3],
+                          f * (UK[4] / rK + (Ss - uK) * (Ss + pK / (rK * (SK - uK))))};
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = FK[v] + SK * (Us[v] - UK[v]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = FK[v];
+    }
+}
+
+// Toro Eq. 4.6-4.7: one side's contribution to the pressure function and derivative
+template <typename R>
+__device__ __forceinline__ void side_f(R p, R rK, R pK, R cK, R g, R &f, R &df)
+{
+    if (p > pK) {
+        const R A = R(2) / ((g + R(1)) * rK);
+        const R B = (g - R(1)) / (g + R(1)) * pK;
+        const R q = sqrt(A / (p + B));
+        f = (p - pK) * q;
+        df = q * (R(1) - R(0.5) * (p - pK) / (B + p));
+    } else {
+        const R z = (g - R(1)) / (R(2) * g);
+        f = R(2) * cK / (g - R(1)) * (pow(p / pK, z) - R(1));
+        df = R(1) / (rK * cK) * pow(p / pK, -(g + R(1)) / (R(2) * g));
+    }
+}
+
+// Exact Riemann problem (Toro Ch. 4).  Returns 0, AMR_ENONPHYSICAL (vacuum) or
+// AMR_ENOCONV; on failure the caller uses HLLC.
+template <typename R>
+__device__ int exact_star(const R WL[NV], const R WR[NV], R g, R tol, int maxit, R &ps, R &us)
+{
+    const R rL = WL[0], uL = WL[1], pL = WL[4];
+    const R rR = WR[0], uR = WR[1], pR = WR[4];
+    const R cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+    const R du = uR - uL;
+    if (R(2) * (cL + cR) / (g - R(1)) <= du) return AMR_ENONPHYSICAL;
+    const R eps = sizeof(R) == 8 ? R(1e-300) : R(1e-37);
+    R p = R(0.5) * (pL + pR) - R(0.125) * du * (rL + rR) * (cL + cR);
+    if (p < eps) p = eps;
+    int it;
+    for (it = 1; it <= maxit; ++it) {
+        R fL, dfL, fR, dfR;
+        side_f(p, rL, pL, cL, g, fL, dfL);
+        side_f(p, rR, pR, cR, g, fR, dfR);
+        R pn = p - (fL + fR + du) / (dfL + dfR);
+        if (pn < eps) pn = eps;
+        const R change = R(2) * fabs(pn - p) / (pn + p);
+        p = pn;
+        if (change < tol) break;
+    }
+    R fL, dfL, fR, dfR;
+    side_f(p, rL, pL, cL, g, fL, dfL);
+    side_f(p, rR, pR, cR, g, fR, dfR);
+    ps = p;
+    us = R(0.5) * (uL + uR) + R(0.5) * (fR - fL);
+    return it > maxit ? AMR_ENOCONV : 0;
+}
+
+// Sampling at x/t = 0 (Toro Sec. 4.5); transverse velocities from the side of the
+// contact the face lies on (left when u* >= 0).
+template <typename R>
+__device__ void exact_sample0(const R WL[NV], const R WR[NV], R g, R ps, R us, R W[NV])
+{
+    const R g1 = (g - R(1)) / (R(2) * g), g2 = (g + R(1)) / (R(2) * g);
+    const R g3 = R(2) * g / (g - R(1)), g4 = R(2) / (g - R(1));
+    const R g5 = R(2) / (g + R(1)), g6 = (g - R(1)) / (g + R(1)), g7 = (g - R(1)) / R(2);
+    const R S = R(0);
+    R rho, u, p;
+    const R *T;
+    if (S <= us) {
+        const R rL = WL[0], uL = WL[1], pL = WL[4], cL = sqrt(g * pL / rL);
+        T = WL;
+        if (ps > pL) {
+            const R SL = uL - cL * sqrt(g2 * ps / pL + g1);
+            if (S <= SL) { rho = rL; u = uL; p = pL; }
+            else { rho = rL * (ps / pL + g6) / (ps / pL * g6 + R(1)); u = us; p = ps; }
+        } else {
+            const R SHL = uL - cL;
+            if (S <= SHL) { rho = rL; u = uL; p = pL; }
+            else {
+                const R cmL = cL * pow(ps / pL, g1);
+                const R STL = us - cmL;
+                if (S > STL) { rho = rL * pow(ps / pL, R(1) / g); u = us; p = ps; }
+                else {
+                    const R c = g5 * (cL + g7 * (uL - S));
+                    rho = rL * pow(c / cL, g4);
+                    u = g5 * (cL + g7 * uL + S);
+                    p = pL * pow(c / cL, g3);
+                }
+            }
+        }
+    } else {
+        const R rR = WR[0], uR = WR[1], pR = WR[4], cR = sqrt(g * pR / rR);
+        T = WR;
+        if (ps > pR) {
+            const R SR = uR + cR * sqrt(g2 * ps / pR + g1);
+            if (S >= SR) { rho = rR; u = uR; p = pR; }
+            else { rho = rR * (ps / pR + g6) / (ps / pR * g6 + R(1)); u = us; p = ps; }
+        } else {
+            const R SHR = uR + cR;
+            if (S >= SHR) { rho = rR; u = uR; p = pR; }
+            else {
+                const R cmR = cR * pow(ps / pR, g1);
+                const R STR = us + cmR;
+                if (S <= STR) { rho = rR * pow(ps / pR, R(1) / g); u = us; p = ps; }
+                else {
+                    const R c = g5 * (cR - g7 * (uR - S));
+                    rho = rR * pow(c / cR, g4);
+                    u = g5 * (-cR + g7 * uR + S);
+                    p = pR * pow(c / cR, g3);
+                }
+            }
+        }
+    }
+    W[0] = rho; W[1] = u; W[2] = T[2]; W[3] = T[3]; W[4] = p;
+}
+
+}  // namespace amr

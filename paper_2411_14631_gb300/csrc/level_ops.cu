@@ -1,0 +1,281 @@
+// Per-level operations around the Godunov update: the CFL time step (newdt_fine,
+// Table 1), refluxing + restriction, initial-state set-up, and the C entry points.
+#include <cfloat>
+#include <cstring>
+#include "hydro_math.cuh"
+
+namespace amr {
+amr_status godunov_dispatch(const amr_tree *t, int level, const hydro_params *p, const double *u_old,
+                            double *u_new, double *reg, const double *dt, double *dt_next, cudaStream_t st);
+
+__device__ __forceinline__ void min_to(double *target, double v)
+{
+    for (int off = 16; off > 0; off >>= 1) {
+        const double o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = o < v ? o : v;
+    }
+    if ((threadIdx.x & 31) == 0 && v < DBL_MAX)
+        atomicMin(reinterpret_cast<unsigned long long *>(target), (unsigned long long)__double_as_longlong(v));
+}
+
+// dt candidate of one cell: cfl * dx / sum_d (|u_d| + c)
+template <typename R>
+__device__ __forceinline__ double cfl_candidate(const double U[NV], double gamma, double rf, double pf, double cfl,
+                                                double dx)
+{
+    Prm<R> p;
+    p.gamma = R(gamma); p.rho_floor = R(rf); p.p_floor = R(pf);
+    R W[NV];
+    cons_to_prim(U, p, W);
+    const R cs = sqrt(p.gamma * W[4] / W[0]);
+    const R sig = (fabs(W[1]) + cs) + (fabs(W[2]) + cs) + (fabs(W[3]) + cs);
+    if (sizeof(R) == 8) return cfl * (dx / double(sig));
+    // FP32: scaled down by (1 - 2^-16) so it never exceeds the FP64 value
+    const float c32 = float(cfl) * (float(dx) / float(sig));
+    return double(c32 * 0.9999847412109375f);
+}
+
+template <typename R>
+__global__ void k_courant(TreeView tv, int64_t cell0, const double *__restrict__ u, double gamma, double rf,
+                          double pf, double cfl, double *dt)
+{
+    const int64_t cell = cell0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    double cand = DBL_MAX;
+    if (cell < tv.ncell && tv.son[cell] < 0) {
+        double U[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = u[v * tv.ncell + cell];
+        cand = cfl_candidate<R>(U, gamma, rf, pf, cfl, ldexp(1.0, -tv.lvl[cell >> 3]));
+    }
+    min_to(dt, cand);
+}
+
+// Coarse level l: leaf cells next to a refined cell take the fine fluxes from the
+// register (-/+ dt/dx * 1/4 * sum of the four fine fluxes); refined cells become the
+// mean of their eight children.
+template <typename R>
+__global__ void k_reflux(TreeView tv, int level, const double *__restrict__ reg, double *u, const double *dtp,
+                         double *dt_next, double gamma, double rf, double pf, double cfl)
+{
+    const int64_t cell = tv.lvl_off[level] * 8 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    double cand = DBL_MAX;
+    if (cell < tv.lvl_off[level + 1] * 8) {
+        const int64_t o = cell >> 3;
+        const int c = int(cell & 7);
+        const int32_t s = tv.son[cell];
+        if (s >= 0) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double sum = 0.0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) sum += u[v * tv.ncell + int64_t(s) * 8 + q];
+                u[v * tv.ncell + cell] = 0.125 * sum;
+            }
+        } else if (reg && level >= tv.levelmin) {
+            const double lam = *dtp / ldexp(1.0, -level);
+            double U[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) U[v] = u[v * tv.ncell + cell];
+            bool hit = false;
+            for (int f = 0; f < 6; ++f) {
+                const int d = f >> 1, side = f & 1;
+                int64_t nb;
+                if (((c >> d) & 1) != side) {
+                    nb = o * 8 + (c ^ (1 << d));
+                } else {
+                    const int32_t N = tv.nbor[6 * o + f];
+                    if (N < 0) continue;                      // outflow face of the box
+                    const int32_t so = tv.son[N];
+                    if (so < 0) continue;                     // coarser neighbour
+                    nb = int64_t(so) * 8 + (c ^ (1 << d));
+                }
+                const int32_t fo = tv.son[nb];
+                if (fo < 0) continue;
+                const int opp = 2 * d + (1 - side);
+                const double *rrow = reg + ((int64_t(fo) - tv.reg_base) * 6 + opp) * NV;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const double corr = 0.25 * rrow[v];
+                    U[v] = side ? U[v] - lam * corr : U[v] + lam * corr;
+                }
+                hit = true;
+            }
+            if (hit) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) u[v * tv.ncell + cell] = U[v];
+                if (dt_next) cand = cfl_candidate<R>(U, gamma, rf, pf, cfl, ldexp(1.0, -level));
+            }
+        }
+    }
+    if (dt_next) min_to(dt_next, cand);
+}
+
+__global__ void k_prim_to_cons(int64_t ncell, const double *__restrict__ w, double *u, double gamma)
+{
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= ncell) return;
+    const double rho = w[i], vx = w[ncell + i], vy = w[2 * ncell + i], vz = w[3 * ncell + i], p = w[4 * ncell + i];
+    u[i] = rho;
+    u[ncell + i] = rho * vx;
+    u[2 * ncell + i] = rho * vy;
+    u[3 * ncell + i] = rho * vz;
+    u[4 * ncell + i] = p / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+}
+
+__global__ void k_cons_to_prim(int64_t ncell, const double *__restrict__ u, double *w, double gamma, double rf, double pf)
+{
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= ncell) return;
+    double U[NV], W[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) U[v] = u[v * ncell + i];
+    Prm<double> p;
+    p.gamma = gamma; p.rho_floor = rf; p.p_floor = pf;
+    cons_to_prim(U, p, W);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v * ncell + i] = W[v];
+}
+
+static amr_status check(const amr_tree *t, const hydro_params *p)
+{
+    if (!t || !p || t->noct <= 0) return AMR_EINVAL;
+    if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->rho_floor > 0.0) || !(p->p_floor > 0.0)) return AMR_EINVAL;
+    if (p->riemann < AMR_RIEMANN_HLLC || p->riemann > AMR_RIEMANN_MLP) return AMR_EINVAL;
+    if (p->precision != AMR_PREC_FP64 && p->precision != AMR_PREC_FP32) return AMR_EINVAL;
+    if (p->tile < 0 || p->tile > 2) return AMR_EINVAL;
+    return AMR_OK;
+}
+
+static amr_status reflux_launch(const amr_tree *t, int level, const hydro_params *p, const double *reg, double *u,
+                                const double *dt, double *dt_next, cudaStream_t st)
+{
+    const int64_t nc = (t->lvl_off[level + 1] - t->lvl_off[level]) * 8;
+    if (nc <= 0) return AMR_OK;
+    const unsigned nb = unsigned((nc + 255) / 256);
+    const TreeView tv = make_view(t);
+    if (p->precision == AMR_PREC_FP32)
+        k_reflux<float><<<nb, 256, 0, st>>>(tv, level, reg, u, dt, dt_next, p->gamma, p->rho_floor, p->p_floor, p->cfl);
+    else
+        k_reflux<double><<<nb, 256, 0, st>>>(tv, level, reg, u, dt, dt_next, p->gamma, p->rho_floor, p->p_floor, p->cfl);
+    AMR_CUDA_TRY(cudaGetLastError());
+    return AMR_OK;
+}
+
+}  // namespace amr
+
+using namespace amr;
+
+extern "C" size_t hydro_flux_reg_bytes(const amr_tree *t)
+{
+    if (!t) return 0;
+    const int64_t rows = t->noct - t->reg_base;
+    return size_t(rows > 0 ? rows : 1) * 6 * NV * sizeof(double);
+}
+
+extern "C" amr_status hydro_init_from_prim(const amr_tree *t, const hydro_params *p, const double *d_w, double *d_u,
+                                           amr_stream stream)
+{
+    if (check(t, p) != AMR_OK || !d_w || !d_u) return AMR_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t nc = 8 * t->noct;
+    k_prim_to_cons<<<unsigned((nc + 255) / 256), 256, 0, st>>>(nc, d_w, d_u, p->gamma);
+    AMR_CUDA_TRY(cudaGetLastError());
+    for (int l = t->levelmax - 1; l >= 1; --l) {
+        amr_status r = reflux_launch(t, l, p, nullptr, d_u, nullptr, nullptr, st);
+        if (r != AMR_OK) return r;
+    }
+    return AMR_OK;
+}
+
+extern "C" amr_status hydro_prim_of_state(const amr_tree *t, const hydro_params *p, const double *d_u, double *d_w,
+                                          amr_stream stream)
+{
+    if (check(t, p) != AMR_OK || !d_w || !d_u) return AMR_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t nc = 8 * t->noct;
+    k_cons_to_prim<<<unsigned((nc + 255) / 256), 256, 0, st>>>(nc, d_u, d_w, p->gamma, p->rho_floor, p->p_floor);
+    AMR_CUDA_TRY(cudaGetLastError());
+    return AMR_OK;
+}
+
+extern "C" amr_status hydro_courant(const amr_tree *t, const hydro_params *p, const double *d_u, double *d_dt,
+                                    amr_stream stream)
+{
+    if (check(t, p) != AMR_OK || !d_u || !d_dt) return AMR_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    AMR_CUDA_TRY(cudaMemsetAsync(d_dt, 0x7F, sizeof(double), st));
+    const TreeView tv = make_view(t);
+    const int64_t c0 = t->lvl_off[t->levelmin] * 8, nc = 8 * t->noct - c0;
+    const unsigned nb = unsigned((nc + 255) / 256);
+    if (p->precision == AMR_PREC_FP32)
+        k_courant<float><<<nb, 256, 0, st>>>(tv, c0, d_u, p->gamma, p->rho_floor, p->p_floor, p->cfl, d_dt);
+    else
+        k_courant<double><<<nb, 256, 0, st>>>(tv, c0, d_u, p->gamma, p->rho_floor, p->p_floor, p->cfl, d_dt);
+    AMR_CUDA_TRY(cudaGetLastError());
+    return AMR_OK;
+}
+
+extern "C" amr_status hydro_godunov_level(const amr_tree *t, int level, const hydro_params *p, const double *d_u_old,
+                                          double *d_u_new, double *d_flux_reg, const double *d_dt, double *d_dt_next,
+                                          amr_stream stream)
+{
+    if (check(t, p) != AMR_OK || !d_u_old || !d_u_new || !d_dt) return AMR_EINVAL;
+    if (p->riemann == AMR_RIEMANN_MLP) return AMR_EINVAL;   // the surrogate runs through its own entry points
+    if (level != -1 && (level < t->levelmin || level > t->levelmax)) return AMR_EINVAL;
+    if (t->levelmax > t->levelmin && !d_flux_reg) return AMR_EINVAL;
+    return godunov_dispatch(t, level, p, d_u_old, d_u_new, d_flux_reg, d_dt, d_dt_next,
+                            reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" amr_status hydro_reflux_level(const amr_tree *t, int level, const hydro_params *p, const double *d_flux_reg,
+                                         double *d_u_new, const double *d_dt, double *d_dt_next, amr_stream stream)
+{
+    if (check(t, p) != AMR_OK || !d_u_new || !d_dt) return AMR_EINVAL;
+    if (level < 1 || level >= t->levelmax) return AMR_EINVAL;
+    if (level >= t->levelmin && !d_flux_reg) return AMR_EINVAL;
+    return reflux_launch(t, level, p, d_flux_reg, d_u_new, d_dt, d_dt_next, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" amr_status hydro_step(const amr_tree *t, const hydro_params *p, const double *d_u_old, double *d_u_new,
+                                 double *d_flux_reg, const double *d_dt, double *d_dt_next, amr_stream stream)
+{
+    if (d_dt_next) AMR_CUDA_TRY(cudaMemsetAsync(d_dt_next, 0x7F, sizeof(double), reinterpret_cast<cudaStream_t>(stream)));
+    amr_status r = hydro_godunov_level(t, -1, p, d_u_old, d_u_new, d_flux_reg, d_dt, d_dt_next, stream);
+    if (r != AMR_OK) return r;
+    for (int l = t->levelmax - 1; l >= 1; --l) {
+        r = reflux_launch(t, l, p, d_flux_reg, d_u_new, d_dt, d_dt_next, reinterpret_cast<cudaStream_t>(stream));
+        if (r != AMR_OK) return r;
+    }
+    return AMR_OK;
+}
+
+extern "C" amr_status amr_get_status(const hydro_params *p, int32_t *h_status, unsigned long long *h_counters)
+{
+    if (!p) return AMR_EINVAL;
+    if (h_status) {
+        *h_status = 0;
+        if (p->d_status) AMR_CUDA_TRY(cudaMemcpy(h_status, p->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    }
+    if (h_counters) {
+        std::memset(h_counters, 0, sizeof(unsigned long long) * AMR_NCOUNTERS);
+        if (p->d_counters)
+            AMR_CUDA_TRY(cudaMemcpy(h_counters, p->d_counters, sizeof(unsigned long long) * AMR_NCOUNTERS,
+                                    cudaMemcpyDeviceToHost));
+    }
+    return AMR_OK;
+}
+
+extern "C" const char *amr_status_string(int s)
+{
+    switch (s) {
+    case AMR_OK: return "ok";
+    case AMR_EINVAL: return "invalid argument";
+    case AMR_EUNBALANCED: return "octree violates the 2:1 rule";
+    case AMR_ECAPACITY: return "caller buffer too small";
+    case AMR_ECUDA: return "CUDA runtime error";
+    case AMR_ETIMEOUT: return "device wait timed out";
+    case AMR_ENONPHYSICAL: return "vacuum in an exact Riemann problem";
+    case AMR_ENOCONV: return "exact Riemann solver did not converge";
+    default: return "unknown status";
+    }
+}

@@ -1,0 +1,368 @@
+// amr_build_octree: the fully threaded octree of Sec. 1 (cells split into eight
+// octants), numbered along the Peano-Hilbert curve, with its neighbour tables and the
+// stencil-slot tables of the oct tiles the hydro kernels update.
+#include <cstring>
+#include <vector>
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+#include "common.cuh"
+
+namespace amr {
+
+constexpr int LMAX_BUILD = 20;          // 3*(l-1) key bits + level must fit 64 bits
+constexpr int32_t UNNEEDED = INT32_MIN + 1;
+
+static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct TreeLayout {
+    size_t lvl, ix, iy, iz, key, son, father, nbor, nb27, refmask, root[2], slot[2], total;
+    int64_t tile_bound[2];
+};
+
+static int nslot(int depth) { const int s = (1 << depth) + 2; return s * s * s; }
+
+static TreeLayout tree_layout(int64_t n, const int64_t cnt[AMR_MAXLEV + 2], int levelmin, int lmax)
+{
+    TreeLayout L;
+    for (int d = 0; d < 2; ++d) {
+        int64_t b = 0;
+        for (int l = levelmin; l <= lmax; ++l) {
+            const int r = l - (d + 1);
+            if (r >= 1) b += cnt[r] < cnt[l] ? cnt[r] : cnt[l];
+        }
+        L.tile_bound[d] = b;
+    }
+    size_t o = 0;
+    auto put = [&](size_t bytes) { size_t at = o; o += al256(bytes); return at; };
+    L.lvl = put(4 * n); L.ix = put(4 * n); L.iy = put(4 * n); L.iz = put(4 * n);
+    L.key = put(8 * n); L.son = put(32 * n); L.father = put(4 * n); L.nbor = put(24 * n);
+    L.nb27 = put(108 * n); L.refmask = put(n);
+    for (int d = 0; d < 2; ++d) {
+        L.root[d] = put(4 * L.tile_bound[d]);
+        L.slot[d] = put(4 * L.tile_bound[d] * nslot(d + 1));
+    }
+    L.total = o;
+    return L;
+}
+
+struct WsLayout { size_t lxyz, sk0, sk1, id0, id1, flag, pos, small, cub, total; size_t cub_bytes; };
+
+static size_t cub_bytes_needed(int64_t n)
+{
+    size_t a = 0, b = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, a, (uint64_t *)nullptr, (uint64_t *)nullptr, (int32_t *)nullptr,
+                                    (int32_t *)nullptr, (int)n, 0, 64);
+    cub::DeviceScan::ExclusiveSum(nullptr, b, (int32_t *)nullptr, (int32_t *)nullptr, (int)n);
+    return a > b ? a : b;
+}
+
+static WsLayout ws_layout(int64_t n)
+{
+    WsLayout W;
+    size_t o = 0;
+    auto put = [&](size_t bytes) { size_t at = o; o += al256(bytes); return at; };
+    W.lxyz = put(16 * n); W.sk0 = put(8 * n); W.sk1 = put(8 * n); W.id0 = put(4 * n); W.id1 = put(4 * n);
+    W.flag = put(4 * (n + 1)); W.pos = put(4 * (n + 1)); W.small = put(1024);
+    W.cub_bytes = cub_bytes_needed(n);
+    W.cub = put(W.cub_bytes);
+    W.total = o;
+    return W;
+}
+
+static amr_status count_levels(const int32_t *h, int64_t n, int64_t cnt[AMR_MAXLEV + 2], int *lmax)
+{
+    for (int l = 0; l < AMR_MAXLEV + 2; ++l) cnt[l] = 0;
+    *lmax = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int l = h[4 * i];
+        if (l < 1 || l > LMAX_BUILD) return AMR_EINVAL;
+        cnt[l]++;
+        if (l > *lmax) *lmax = l;
+    }
+    return AMR_OK;
+}
+
+static amr_status check_geom(const amr_geom *g, int64_t n)
+{
+    if (!g || n <= 0 || n > (int64_t(1) << 27)) return AMR_EINVAL;   // 8*noct < 2^31 - 2
+    if (g->levelmin < 2 || g->levelmin > LMAX_BUILD) return AMR_EINVAL;
+    for (int f = 0; f < 6; ++f)
+        if (g->bc[f] != AMR_BC_PERIODIC && g->bc[f] != AMR_BC_OUTFLOW) return AMR_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if ((g->bc[2 * a] == AMR_BC_PERIODIC) != (g->bc[2 * a + 1] == AMR_BC_PERIODIC)) return AMR_EINVAL;
+    return AMR_OK;
+}
+
+// ---- kernels --------------------------------------------------------------------
+__global__ void k_keys(const int32_t *__restrict__ lxyz, int64_t n, uint64_t *sk, int32_t *id, int32_t *err)
+{
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const int l = lxyz[4 * i];
+    const int32_t x = lxyz[4 * i + 1], y = lxyz[4 * i + 2], z = lxyz[4 * i + 3];
+    const int64_t m = int64_t(1) << (l - 1);
+    if (x < 0 || y < 0 || z < 0 || x >= m || y >= m || z >= m) {
+        set_error(err, AMR_EINVAL);
+        sk[i] = ~uint64_t(0);
+    } else {
+        sk[i] = (uint64_t(l) << 58) | hilbert3(l - 1, x, y, z);
+    }
+    id[i] = int32_t(i);
+}
+
+__global__ void k_scatter(const uint64_t *__restrict__ sk, const int32_t *__restrict__ id,
+                          const int32_t *__restrict__ lxyz, int64_t n, int32_t *lvl, int32_t *ix, int32_t *iy,
+                          int32_t *iz, uint64_t *key, int32_t *err)
+{
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const int32_t s = id[i];
+    lvl[i] = lxyz[4 * s];
+    ix[i] = lxyz[4 * s + 1];
+    iy[i] = lxyz[4 * s + 2];
+    iz[i] = lxyz[4 * s + 3];
+    key[i] = sk[i] & ((uint64_t(1) << 58) - 1);
+    if (i > 0 && sk[i] == sk[i - 1]) set_error(err, AMR_EINVAL);   // duplicate oct
+}
+
+struct BuildView {
+    int64_t n;
+    int32_t levelmin, levelmax;
+    int32_t bc[6];
+    int64_t lvl_off[AMR_MAXLEV + 2];
+    const int32_t *lvl, *ix, *iy, *iz;
+    const uint64_t *key;
+};
+
+// level-l cell (X,Y,Z) (inside the box) -> cell id, or -1 if its oct is absent
+__device__ int64_t cell_of(const BuildView &b, int l, int64_t X, int64_t Y, int64_t Z)
+{
+    const int64_t o = find_oct(b.key, b.lvl_off, l, X >> 1, Y >> 1, Z >> 1);
+    return o < 0 ? -1 : o * 8 + (X & 1) + 2 * (Y & 1) + 4 * (Z & 1);
+}
+
+__global__ void k_tables(BuildView b, int32_t *son, int32_t *father, int32_t *nbor, int32_t *nb27,
+                         uint8_t *refmask, int32_t *err)
+{
+    const int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (o >= b.n) return;
+    const int l = b.lvl[o];
+    const int64_t x = b.ix[o], y = b.iy[o], z = b.iz[o];
+    uint32_t mask = 0;
+    for (int c = 0; c < 8; ++c) {
+        const int64_t s = find_oct(b.key, b.lvl_off, l + 1, 2 * x + (c & 1), 2 * y + ((c >> 1) & 1), 2 * z + ((c >> 2) & 1));
+        son[8 * o + c] = int32_t(s);
+        if (s >= 0) mask |= 1u << c;
+    }
+    refmask[o] = uint8_t(mask);
+    if (l < b.levelmin && mask != 0xFFu) set_error(err, AMR_EINVAL);   // levels below levelmin have no leaves
+    if (l == 1) {
+        father[o] = -1;
+        for (int k = 0; k < 6; ++k) nbor[6 * o + k] = -1;
+        for (int k = 0; k < 27; ++k) nb27[27 * o + k] = (k == 13) ? int32_t(o) : OUTSIDE;
+        return;
+    }
+    const int64_t f = cell_of(b, l - 1, x, y, z);
+    if (f < 0) set_error(err, AMR_EINVAL);                             // oct without its father cell
+    father[o] = int32_t(f);
+    const int64_t nf = int64_t(1) << (l - 1);
+    for (int k = 0; k < 6; ++k) {
+        int64_t P[3] = {x, y, z};
+        P[k >> 1] += (k & 1) ? 1 : -1;
+        int out = 0;
+        for (int a = 0; a < 3; ++a) out |= bc_apply(b.bc, a, nf, P[a]);
+        if (out) { nbor[6 * o + k] = -1; continue; }
+        const int64_t cid = cell_of(b, l - 1, P[0], P[1], P[2]);
+        if (cid < 0) set_error(err, AMR_EUNBALANCED);
+        nbor[6 * o + k] = int32_t(cid);
+    }
+    for (int k = 0; k < 27; ++k) {
+        const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+        int64_t P[3] = {x + dx, y + dy, z + dz};
+        int out = 0;
+        for (int a = 0; a < 3; ++a) out |= bc_apply(b.bc, a, nf, P[a]);
+        if (out) { nb27[27 * o + k] = OUTSIDE; continue; }
+        const int64_t cid = cell_of(b, l - 1, P[0], P[1], P[2]);   // 2:1 rule: must exist
+        if (cid < 0) { set_error(err, AMR_EUNBALANCED); nb27[27 * o + k] = OUTSIDE; continue; }
+        const int64_t s = find_oct(b.key, b.lvl_off, l, P[0], P[1], P[2]);
+        nb27[27 * o + k] = s >= 0 ? int32_t(s) : int32_t(-1 - cid);
+    }
+}
+
+// flag octs that root a tile of the given depth: a descendant `depth` levels down
+__global__ void k_tile_flags(BuildView b, const int32_t *__restrict__ son, const uint8_t *__restrict__ refmask,
+                             int depth, int32_t *flag)
+{
+    const int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (o > b.n) return;
+    if (o == b.n) { flag[o] = 0; return; }
+    const int l = b.lvl[o] + depth;   // level the tile updates
+    int f = 0;
+    if (l >= b.levelmin && l <= b.levelmax) {
+        if (depth == 1) {
+            f = refmask[o] != 0;
+        } else {
+            for (int c = 0; c < 8; ++c) {
+                const int32_t s = son[8 * o + c];
+                if (s >= 0 && refmask[s] != 0) f = 1;
+            }
+        }
+    }
+    flag[o] = f;
+}
+
+__global__ void k_tile_compact(int64_t n, const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
+                               int32_t *root)
+{
+    const int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (o < n && flag[o]) root[pos[o]] = int32_t(o);
+}
+
+// tiles updating level l are the compacted roots at level l - depth:
+// [pos[lvl_off[l - depth]], pos[lvl_off[l - depth + 1]])
+__global__ void k_tile_counts(BuildView b, const int32_t *__restrict__ pos, int depth, int64_t *out)
+{
+    const int l = threadIdx.x;
+    if (l >= AMR_MAXLEV + 2) return;
+    const int r = l - depth < 0 ? 0 : l - depth;
+    const int64_t at = b.lvl_off[r] < b.n ? b.lvl_off[r] : b.n;
+    out[l] = pos[at];
+}
+
+// Stencil slots of each tile: a depth-D tile covers 2^D x 2^D x 2^D level-l octs and
+// its stencil (2^D + 2)^3 oct positions, one layer of octs (two cells) around it.
+__global__ void k_tile_slots(BuildView b, int depth, int64_t ntile, const int32_t *__restrict__ root,
+                             const int32_t *__restrict__ son, int32_t *slot)
+{
+    const int ns = (1 << depth) + 2, nsl = ns * ns * ns;
+    const int64_t gi = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (gi >= ntile * nsl) return;
+    const int64_t t = gi / nsl;
+    const int s = int(gi % nsl);
+    const int32_t r = root[t];
+    const int l = b.lvl[r] + depth;
+    const int sx = s % ns, sy = (s / ns) % ns, sz = s / (ns * ns);
+    // level-l oct coordinates == level-(l-1) father cell coordinates
+    int64_t P[3] = {int64_t(b.ix[r]) * (1 << depth) - 1 + sx, int64_t(b.iy[r]) * (1 << depth) - 1 + sy,
+                    int64_t(b.iz[r]) * (1 << depth) - 1 + sz};
+    const int64_t nf = int64_t(1) << (l - 1);
+    int out = 0;
+    for (int a = 0; a < 3; ++a) out |= bc_apply(b.bc, a, nf, P[a]);
+    int32_t v;
+    if (out) {
+        v = OUTSIDE;
+    } else {
+        const int64_t F = cell_of(b, l - 1, P[0], P[1], P[2]);
+        if (F < 0) v = UNNEEDED;                    // no updated oct of the tile reaches it (2:1 rule)
+        else v = son[F] >= 0 ? son[F] : int32_t(-1 - F);
+    }
+    slot[gi] = v;
+}
+
+}  // namespace amr
+
+using namespace amr;
+
+extern "C" amr_status amr_build_octree_query(const amr_geom *geom, const int32_t *h_oct_lxyz, int64_t n_oct,
+                                             size_t *tree_bytes, size_t *workspace_bytes)
+{
+    if (check_geom(geom, n_oct) != AMR_OK || !h_oct_lxyz || !tree_bytes || !workspace_bytes) return AMR_EINVAL;
+    int64_t cnt[AMR_MAXLEV + 2];
+    int lmax;
+    if (count_levels(h_oct_lxyz, n_oct, cnt, &lmax) != AMR_OK) return AMR_EINVAL;
+    *tree_bytes = tree_layout(n_oct, cnt, geom->levelmin, lmax).total;
+    *workspace_bytes = ws_layout(n_oct).total;
+    return AMR_OK;
+}
+
+extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oct_lxyz, int64_t n,
+                                       void *d_tree_mem, size_t tree_bytes, void *d_workspace,
+                                       size_t workspace_bytes, amr_tree *out, amr_stream stream)
+{
+    if (check_geom(geom, n) != AMR_OK || !h_oct_lxyz || !d_tree_mem || !d_workspace || !out) return AMR_EINVAL;
+    if ((uintptr_t(d_tree_mem) & 255) || (uintptr_t(d_workspace) & 255)) return AMR_EINVAL;
+    int64_t cnt[AMR_MAXLEV + 2];
+    int lmax;
+    if (count_levels(h_oct_lxyz, n, cnt, &lmax) != AMR_OK) return AMR_EINVAL;
+    const int lmin = geom->levelmin;
+    if (lmax < lmin) return AMR_EINVAL;
+    for (int l = 1; l <= lmin; ++l)
+        if (cnt[l] != (int64_t(1) << (3 * (l - 1)))) return AMR_EINVAL;   // levels 1..levelmin complete
+    const TreeLayout L = tree_layout(n, cnt, lmin, lmax);
+    const WsLayout W = ws_layout(n);
+    if (tree_bytes < L.total || workspace_bytes < W.total) return AMR_ECAPACITY;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *T = static_cast<char *>(d_tree_mem), *S = static_cast<char *>(d_workspace);
+
+    std::memset(out, 0, sizeof(*out));
+    out->noct = n;
+    out->levelmin = lmin;
+    out->levelmax = lmax;
+    for (int f = 0; f < 6; ++f) out->bc[f] = geom->bc[f];
+    int64_t acc = 0;
+    for (int l = 0; l < AMR_MAXLEV + 2; ++l) { out->lvl_off[l] = acc; acc += (l <= AMR_MAXLEV) ? cnt[l] : 0; }
+    out->lvl_off[AMR_MAXLEV + 1] = n;
+    out->reg_base = out->lvl_off[lmin + 1];
+    out->lvl = (int32_t *)(T + L.lvl); out->ix = (int32_t *)(T + L.ix); out->iy = (int32_t *)(T + L.iy);
+    out->iz = (int32_t *)(T + L.iz); out->key = (uint64_t *)(T + L.key); out->son = (int32_t *)(T + L.son);
+    out->father = (int32_t *)(T + L.father); out->nbor = (int32_t *)(T + L.nbor);
+    out->nb27 = (int32_t *)(T + L.nb27); out->refmask = (uint8_t *)(T + L.refmask);
+    for (int d = 0; d < 2; ++d) {
+        out->tile_root[d] = (int32_t *)(T + L.root[d]);
+        out->tile_slot[d] = (int32_t *)(T + L.slot[d]);
+    }
+    int32_t *lxyz = (int32_t *)(S + W.lxyz);
+    uint64_t *sk0 = (uint64_t *)(S + W.sk0), *sk1 = (uint64_t *)(S + W.sk1);
+    int32_t *id0 = (int32_t *)(S + W.id0), *id1 = (int32_t *)(S + W.id1);
+    int32_t *flag = (int32_t *)(S + W.flag), *pos = (int32_t *)(S + W.pos);
+    int32_t *err = (int32_t *)(S + W.small);
+    int64_t *tcnt = (int64_t *)(S + W.small + 256);
+    void *cubtmp = S + W.cub;
+
+    AMR_CUDA_TRY(cudaMemcpyAsync(lxyz, h_oct_lxyz, 16 * size_t(n), cudaMemcpyHostToDevice, st));
+    AMR_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+    const int TB = 256;
+    const unsigned nb = unsigned((n + TB - 1) / TB), nb1 = unsigned((n + TB) / TB);
+    k_keys<<<nb, TB, 0, st>>>(lxyz, n, sk0, id0, err);
+    size_t cb = W.cub_bytes;
+    AMR_CUDA_TRY(cub::DeviceRadixSort::SortPairs(cubtmp, cb, sk0, sk1, id0, id1, (int)n, 0, 64, st));
+    k_scatter<<<nb, TB, 0, st>>>(sk1, id1, lxyz, n, out->lvl, out->ix, out->iy, out->iz, out->key, err);
+
+    BuildView bv;
+    bv.n = n; bv.levelmin = lmin; bv.levelmax = lmax;
+    for (int f = 0; f < 6; ++f) bv.bc[f] = geom->bc[f];
+    for (int l = 0; l < AMR_MAXLEV + 2; ++l) bv.lvl_off[l] = out->lvl_off[l];
+    bv.lvl = out->lvl; bv.ix = out->ix; bv.iy = out->iy; bv.iz = out->iz; bv.key = out->key;
+    k_tables<<<nb, TB, 0, st>>>(bv, out->son, out->father, out->nbor, out->nb27, out->refmask, err);
+
+    for (int d = 0; d < 2; ++d) {
+        const int depth = d + 1;
+        k_tile_flags<<<nb1, TB, 0, st>>>(bv, out->son, out->refmask, depth, flag);
+        cb = W.cub_bytes;
+        AMR_CUDA_TRY(cub::DeviceScan::ExclusiveSum(cubtmp, cb, flag, pos, (int)(n + 1), st));
+        k_tile_compact<<<nb, TB, 0, st>>>(n, flag, pos, out->tile_root[d]);
+        k_tile_counts<<<1, 32, 0, st>>>(bv, pos, depth, tcnt + d * 32);
+    }
+    int64_t hc[64];
+    int32_t herr = 0;
+    AMR_CUDA_TRY(cudaMemcpyAsync(hc, tcnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    AMR_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st));
+    AMR_CUDA_TRY(cudaStreamSynchronize(st));
+    AMR_CUDA_TRY(cudaGetLastError());
+    if (herr != 0) return amr_status(herr);
+    for (int d = 0; d < 2; ++d) {
+        for (int l = 0; l < AMR_MAXLEV + 2; ++l) out->tile_off[d][l] = hc[d * 32 + l];
+        const int64_t ntile = out->tile_off[d][AMR_MAXLEV + 1];
+        if (ntile > L.tile_bound[d]) return AMR_ECAPACITY;
+        if (ntile > 0) {
+            const int64_t tot = ntile * nslot(d + 1);
+            k_tile_slots<<<unsigned((tot + TB - 1) / TB), TB, 0, st>>>(bv, d + 1, ntile, out->tile_root[d], out->son,
+                                                                      out->tile_slot[d]);
+        }
+    }
+    AMR_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st));
+    AMR_CUDA_TRY(cudaStreamSynchronize(st));
+    AMR_CUDA_TRY(cudaGetLastError());
+    if (herr != 0) return amr_status(herr);
+    return AMR_OK;
+}

@@ -1,0 +1,80 @@
+"""The C ABI library loads and exports every entry point include/amrhydro.h declares,
+and the ctypes mirror of its structs has the C layout (no GPU needed)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ \*]*?\b([a-z_][a-z0-9_]*)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2411_14631_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(\S+)", out))
+    declared = _declared()
+    assert len(declared) >= 11
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_covers_header(built):
+    from paper_2411_14631_gb300 import abi
+    L = abi.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+    assert set(abi.EXPORTS) <= set(_declared())
+    assert L.amr_status_string(abi.EUNBALANCED) == b"octree violates the 2:1 rule"
+
+
+def test_struct_layout_matches_c(tmp_path):
+    import ctypes as C
+    from paper_2411_14631_gb300 import abi
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "amrhydro.h"\n'
+                   'int main(){printf("%zu %zu %zu %zu %zu\\n", sizeof(amr_tree), sizeof(hydro_params),'
+                   ' sizeof(amr_geom), offsetof(amr_tree, tile_slot), offsetof(hydro_params, d_counters));}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [C.sizeof(abi.AmrTree), C.sizeof(abi.HydroParams), C.sizeof(abi.AmrGeom),
+                   abi.AmrTree.tile_slot.offset, abi.HydroParams.d_counters.offset]
+
+
+def test_query_is_host_only_and_validates(built):
+    import ctypes as C
+    import numpy as np
+    from paper_2411_14631_gb300 import abi, workloads as W
+    lx = W.uniform_tree(4)
+    g = abi.AmrGeom(4, (C.c_int32 * 6)(*([1] * 6)))
+    tb, wb = C.c_size_t(), C.c_size_t()
+    assert abi.lib().amr_build_octree_query(C.byref(g), lx.ctypes.data_as(C.c_void_p), lx.shape[0],
+                                            C.byref(tb), C.byref(wb)) == abi.OK
+    assert tb.value > 0 and wb.value > 0
+    g.levelmin = 1
+    assert abi.lib().amr_build_octree_query(C.byref(g), lx.ctypes.data_as(C.c_void_p), lx.shape[0],
+                                            C.byref(tb), C.byref(wb)) == abi.EINVAL
+    g.levelmin = 4
+    g.bc[0] = 0   # periodic on one face of an axis only
+    assert abi.lib().amr_build_octree_query(C.byref(g), lx.ctypes.data_as(C.c_void_p), lx.shape[0],
+                                            C.byref(tb), C.byref(wb)) == abi.EINVAL
+    bad = lx.copy(); bad[0, 0] = 25
+    g.bc[0] = 1
+    assert abi.lib().amr_build_octree_query(C.byref(g), bad.ctypes.data_as(C.c_void_p), bad.shape[0],
+                                            C.byref(tb), C.byref(wb)) == abi.EINVAL

@@ -1,0 +1,227 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Integer tables: bit-exact.  FP64 fields: per field max|gpu - oracle| / max|oracle|
+<= 1e-12 (the tolerance stated for the FP64 GPU path; the kernels may contract
+multiply-adds, the oracle does not).  FP32 path: L1 distance from the FP64 oracle
+bounded (reconstruction and Riemann solve in FP32, state accumulation in FP64)."""
+import numpy as np
+import pytest
+
+from paper_2411_14631_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+OUT, PER = (1,) * 6, (0,) * 6
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_14631_gb300 import build
+    build.build()
+    from paper_2411_14631_gb300 import hydro
+    return hydro
+
+
+def _smooth_random(xyz, seed, amp=0.3):
+    rng = np.random.default_rng(seed)
+    Wp = np.empty((5, xyz.shape[0]))
+    ph = rng.uniform(0, 2 * np.pi, (5, 3))
+    for v in range(5):
+        s = sum(np.sin(2 * np.pi * xyz[:, d] + ph[v, d]) for d in range(3))
+        Wp[v] = s * (amp if v in (0, 4) else 0.5)
+    Wp[0] = 1.0 + Wp[0]
+    Wp[4] = 1.5 + Wp[4]
+    return Wp
+
+
+def _pair(oracle, H, lx, levelmin, bc, prims, gamma, cfl=0.8, riemann=0, precision=0, tile=0):
+    import torch
+    t = oracle.Tree(lx, levelmin, bc)
+    assert t.ok
+    g = H.Octree(lx, levelmin, bc)
+    xyz, _ = t.cell_centres()
+    w0 = prims(xyz)
+    prm_o = oracle.params(gamma=gamma, cfl=cfl, riemann=riemann)
+    prm_g = H.Params(gamma, cfl=cfl, riemann=riemann, precision=precision, tile=tile)
+    u_o = t.init_from_prim(w0, prm_o)
+    sim = H.Simulation(g, prm_g, w0=w0)
+    torch.cuda.synchronize()
+    return t, g, prm_o, prm_g, u_o, sim
+
+
+def _relerr(a, b):
+    return np.array([np.max(np.abs(a[v] - b[v])) / max(np.max(np.abs(b[v])), 1e-300) for v in range(5)])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_octree_tables_bit_exact(oracle, H, seed):
+    rng = np.random.default_rng(200 + seed)
+    base = int(rng.integers(2, 4)); extra = int(rng.integers(1, 4))
+    periodic = bool(seed % 2)
+    lx = W.random_tree(base, extra, seed, p_refine=0.25, periodic=periodic)
+    rng.shuffle(lx)                       # input order must not matter
+    bc = PER if periodic else OUT
+    t = oracle.Tree(lx, base, bc)
+    g = H.Octree(lx, base, bc)
+    tab = {k: v.cpu().numpy() for k, v in g.tables().items()}
+    for k in ("lvl", "ix", "iy", "iz", "son", "father", "nbor", "nb27"):
+        assert np.array_equal(tab[k], getattr(t, k)), k
+    assert np.array_equal(tab["key"].view(np.uint64), t.key)
+    assert np.array_equal(g.lvl_off[:22], t.lvl_off[:22])
+    refm = (t.son.reshape(-1, 8) >= 0) @ (1 << np.arange(8))
+    assert np.array_equal(tab["refmask"], refm.astype(np.uint8))
+
+
+def test_octree_errors(oracle, H):
+    from paper_2411_14631_gb300 import abi
+    levels = {l: W.full_level(l) for l in range(1, 4)}
+    levels[4] = W._pack(np.array([0]), np.array([0]), np.array([0]))
+    levels[5] = W._pack(np.array([1]), np.array([1]), np.array([1]))
+    with pytest.raises(abi.AmrError) as e:
+        H.Octree(W.to_lxyz(levels), 3)
+    assert e.value.status == abi.EUNBALANCED
+    lx = W.uniform_tree(3)
+    with pytest.raises(abi.AmrError) as e:
+        H.Octree(np.concatenate([lx, lx[-1:]]), 3)
+    assert e.value.status == abi.EINVAL
+    with pytest.raises(abi.AmrError) as e:
+        H.Octree(lx[:-1], 3)
+    assert e.value.status == abi.EINVAL
+
+
+def _run_both(t, prm_o, u_o, sim, nsteps):
+    import torch
+    dts = []
+    for _ in range(nsteps):
+        dt_g = float(sim.dt.item())
+        u_o, dt_o, st = t.step(u_o, prm_o)
+        assert st == 0
+        dts.append((dt_o, dt_g))
+        sim.step()
+    torch.cuda.synchronize()
+    return u_o, sim.u.cpu().numpy(), dts
+
+
+def test_sod_32cubed_fp64_parity(oracle, H):
+    """Sod shock tube, 32^3 at level 5 (4096 octs), outflow, HLLC, CFL 0.8, 20 steps."""
+    t, g, prm_o, prm_g, u_o, sim = _pair(oracle, H, W.uniform_tree(5), 5, OUT, lambda x: W.sod_prims(x), 1.4)
+    u_o, u_g, dts = _run_both(t, prm_o, u_o, sim, 20)
+    for dt_o, dt_g in dts:
+        assert abs(dt_o - dt_g) <= 1e-14 * dt_o
+    assert np.all(_relerr(u_g, u_o) <= FP64_TOL), _relerr(u_g, u_o)
+    assert prm_g.read_status()[0] == 0
+
+
+@pytest.mark.parametrize("seed,periodic", [(0, True), (1, False), (2, True), (3, False)])
+def test_amr_fp64_parity(oracle, H, seed, periodic):
+    """Random balanced AMR trees (up to 3 levels of refinement): ghost interpolation,
+    flux register, refluxing and restriction against the oracle."""
+    lx = W.random_tree(3, 3, 50 + seed, p_refine=0.3, periodic=periodic)
+    t, g, prm_o, prm_g, u_o, sim = _pair(oracle, H, lx, 3, PER if periodic else OUT,
+                                        lambda x: _smooth_random(x, seed), 5 / 3, cfl=0.6)
+    assert t.levelmax >= 5
+    u_o, u_g, dts = _run_both(t, prm_o, u_o, sim, 4)
+    for dt_o, dt_g in dts:
+        assert abs(dt_o - dt_g) <= 1e-14 * dt_o
+    err = _relerr(u_g, u_o)
+    assert np.all(err <= FP64_TOL), err
+
+
+def test_exact_riemann_fp64_parity(oracle, H):
+    lx = W.random_tree(3, 2, 7, p_refine=0.3, periodic=False)
+    t, g, prm_o, prm_g, u_o, sim = _pair(oracle, H, lx, 3, OUT, lambda x: W.sod_prims(x, 1), 1.4, riemann=1)
+    u_o, u_g, _ = _run_both(t, prm_o, u_o, sim, 5)
+    err = _relerr(u_g, u_o)
+    assert np.all(err <= FP64_TOL), err
+
+
+def test_single_level_calls_match_step(oracle, H):
+    """hydro_godunov_level per level + hydro_reflux_level per level == hydro_step."""
+    import torch
+    lx = W.random_tree(3, 2, 9, p_refine=0.3, periodic=True)
+    t, g, prm_o, prm_g, u_o, sim = _pair(oracle, H, lx, 3, PER, lambda x: _smooth_random(x, 5), 5 / 3)
+    u_new = torch.empty_like(sim.u)
+    reg = torch.zeros_like(sim.reg)
+    for l in range(g.levelmin, g.levelmax + 1):
+        H.hydro_godunov_level(g, l, prm_g, sim.u, u_new, reg, sim.dt)
+    for l in range(g.levelmax - 1, 0, -1):
+        H.hydro_reflux_level(g, l, prm_g, reg, u_new, sim.dt)
+    sim.step()
+    assert torch.equal(u_new, sim.u)
+
+
+def _l1(t, a, b):
+    leaf = t.son < 0
+    vol = np.ldexp(1.0, -3 * np.repeat(t.lvl, 8).astype(np.int64))[leaf]
+    return np.array([np.sum(np.abs(a[v, leaf] - b[v, leaf]) * vol) / np.sum(np.abs(b[v, leaf]) * vol + 1e-300)
+                     for v in range(5)])
+
+
+@pytest.mark.parametrize("tile", [1, 2])
+def test_fp32_path_close_to_oracle(oracle, H, tile):
+    """FP32 reconstruction + Riemann with FP64 accumulation stays within FP32 round-off
+    growth of the FP64 oracle on a smooth AMR flow."""
+    lx = W.random_tree(3, 2, 21, p_refine=0.3, periodic=True)
+    t, g, prm_o, prm_g, u_o, sim = _pair(oracle, H, lx, 3, PER, lambda x: _smooth_random(x, 8), 5 / 3,
+                                        cfl=0.6, precision=1, tile=tile)
+    import torch
+    u_o2 = u_o.copy()
+    for _ in range(5):
+        sim.step()
+    torch.cuda.synchronize()
+    for _ in range(5):
+        u_o2, _, _ = t.step(u_o2, prm_o)
+    l1 = _l1(t, sim.u.cpu().numpy(), u_o2)
+    assert np.all(l1[[0, 4]] < 1e-5), l1
+
+
+def test_fp32_tile_depth_invariance(oracle, H):
+    """The tile a cell is updated in does not change its arithmetic: depth-1 and depth-2
+    tiles give bitwise identical states."""
+    import torch
+    lx = W.random_tree(3, 2, 31, p_refine=0.4, periodic=False)
+    res = []
+    for tile in (1, 2):
+        t, g, prm_o, prm_g, u_o, sim = _pair(oracle, H, lx, 3, OUT, lambda x: _smooth_random(x, 2), 5 / 3,
+                                            precision=1, tile=tile)
+        for _ in range(3):
+            sim.step()
+        torch.cuda.synchronize()
+        res.append(sim.u.cpu().numpy())
+    assert np.array_equal(res[0], res[1])
+
+
+def test_conservation_fp64_and_fp32(oracle, H):
+    import torch
+    lx = W.random_tree(3, 2, 41, p_refine=0.3, periodic=True)
+    for precision in (0, 1):
+        t, g, prm_o, prm_g, u_o, sim = _pair(oracle, H, lx, 3, PER, lambda x: _smooth_random(x, 3), 5 / 3,
+                                            cfl=0.5, precision=precision)
+        leaf = t.son < 0
+        vol = np.ldexp(1.0, -3 * np.repeat(t.lvl, 8).astype(np.int64))[leaf]
+        tot = lambda u: np.array([np.sum(u[v, leaf] * vol) for v in range(5)])
+        scale = tot(np.abs(u_o))
+        t0 = tot(sim.u.cpu().numpy())
+        for _ in range(5):
+            sim.step()
+        torch.cuda.synchronize()
+        drift = np.abs(tot(sim.u.cpu().numpy()) - t0) / scale
+        limit = 5e-13 if precision == 0 else 1e-9
+        assert np.all(drift < limit), (precision, drift)
+
+
+def test_uniform_flow_preserved(oracle, H):
+    import torch
+    for precision in (0, 1):
+        t, g, prm_o, prm_g, u_o, sim = _pair(oracle, H, W.uniform_tree(4), 4, PER,
+                                            lambda x: W.uniform_prims(x, 1.3, (0.4, -0.7, 0.2), 0.9), 5 / 3,
+                                            precision=precision)
+        u0 = sim.u.clone()
+        for _ in range(3):
+            sim.step()
+        torch.cuda.synchronize()
+        assert torch.equal(sim.u, u0)

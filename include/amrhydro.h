@@ -99,6 +99,9 @@ typedef struct {
     int32_t *nbor;                          /* per oct x 6: father-level face-neighbour cell, -1 beyond an outflow face */
     int32_t *nb27;                          /* per oct x 27: same-level neighbour oct, -(1+coarse cell), or INT32_MIN beyond an outflow face */
     uint8_t *refmask;                       /* per oct: bit c set iff cell c is refined */
+    uint8_t *fused;                         /* per oct: 1 iff its father cell is restricted inside
+                                               hydro_godunov_level (all eight cells leaves, none next
+                                               to a refined cell), 0 if hydro_reflux_level does it */
     int32_t *tile_root[2];                  /* per tile: root oct (level l-d-1) */
     int32_t *tile_slot[2];                  /* per tile: (2^(d+1)+2)^3 stencil slots */
 } amr_tree;
@@ -136,8 +139,10 @@ amr_status hydro_courant(const amr_tree *tree, const hydro_params *params, const
 /* godunov_fine (Table 1) for one level (level >= levelmin) or for every level in one
    launch (level = -1): for every oct of the level(s), gather the ghosted stencil
    (interpolating from the coarser level where a neighbour is absent), MUSCL-Hancock
-   predictor, Riemann solve at every face, conservative update into d_u_new (all cells
-   of the level's octs), and flux-register rows (d_flux_reg, hydro_flux_reg_bytes) for
+   predictor, Riemann solve at every face, conservative update into d_u_new (every leaf
+   cell of the level's octs, plus the father cells of octs flagged in tree->fused: the
+   mean of their eight new children; other refined cells are left to the restriction of
+   hydro_reflux_level), and flux-register rows (d_flux_reg, hydro_flux_reg_bytes) for
    oct sides that face a coarser leaf.  Faces whose other side is a refined cell carry
    no flux here.  d_dt: device scalar time step (read, not written).  d_dt_next: if not
    NULL, receives atomically min(*d_dt_next, cfl * dx / sum(|u_d|+c)) over the leaf

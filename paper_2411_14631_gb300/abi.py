@@ -37,7 +37,8 @@ class AmrTree(C.Structure):
                 ("reg_base", C.c_int64),
                 ("lvl", C.c_void_p), ("ix", C.c_void_p), ("iy", C.c_void_p), ("iz", C.c_void_p),
                 ("key", C.c_void_p), ("son", C.c_void_p), ("father", C.c_void_p), ("nbor", C.c_void_p),
-                ("nb27", C.c_void_p), ("refmask", C.c_void_p), ("tile_root", C.c_void_p * 2),
+                ("nb27", C.c_void_p), ("refmask", C.c_void_p), ("fused", C.c_void_p),
+                ("tile_root", C.c_void_p * 2),
                 ("tile_slot", C.c_void_p * 2)]
 
 

@@ -8,7 +8,9 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libamrhydro.so")
-SOURCES = ["octree.cu", "godunov.cu", "level_ops.cu"]
+SOURCES = ["octree.cu", "godunov_fp64.cu", "godunov_fp32.cu", "level_ops.cu"]
+# per-file extra flags: the FP32 kernels use fast single-precision division / square root
+EXTRA = {"godunov_fp32.cu": ["--use_fast_math"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(HERE, "..", "include")]
 
@@ -45,7 +47,7 @@ def build(force=False, verbose=False):
 
     def one(src):
         obj = os.path.join(bdir, src.replace(".cu", ".o"))
-        cmd = [exe] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [exe] + ARCH + FLAGS + EXTRA.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))

@@ -94,8 +94,8 @@ struct TreeView {
     int64_t lvl_off[AMR_MAXLEV + 2];
     int64_t reg_base;
     const int32_t *lvl, *ix, *iy, *iz;
-    const int32_t *son, *nbor;
-    const uint8_t *refmask;
+    const int32_t *son, *nbor, *father;
+    const uint8_t *refmask, *fused;
 };
 
 inline TreeView make_view(const amr_tree *t)
@@ -109,7 +109,7 @@ inline TreeView make_view(const amr_tree *t)
     for (int i = 0; i < AMR_MAXLEV + 2; ++i) v.lvl_off[i] = t->lvl_off[i];
     v.reg_base = t->reg_base;
     v.lvl = t->lvl; v.ix = t->ix; v.iy = t->iy; v.iz = t->iz;
-    v.son = t->son; v.nbor = t->nbor; v.refmask = t->refmask;
+    v.son = t->son; v.nbor = t->nbor; v.father = t->father; v.refmask = t->refmask; v.fused = t->fused;
     return v;
 }
 

@@ -10,6 +10,7 @@
 //   3 one Riemann solve per face touching an updated cell;
 //   4 FP64 conservative update of the tile's existing octs, fused CFL candidate for the
 //     next step, and flux-register rows for oct sides facing coarser leaves.
+#pragma once
 #include <cfloat>
 #include "hydro_math.cuh"
 
@@ -66,7 +67,7 @@ __device__ __forceinline__ int64_t coarse_neighbour(const TreeView &tv, int64_t 
 }
 
 // child c of coarse leaf cell F: U_F + sum_d s_d/4 minmod(U_F - U_{F-e_d}, U_{F+e_d} - U_F)
-__device__ void interp_child(const TreeView &tv, const double *__restrict__ u, int64_t F, int c, double out[NV])
+static __device__ void interp_child(const TreeView &tv, const double *__restrict__ u, int64_t F, int c, double out[NV])
 {
     const int64_t oF = F >> 3;
     const int cf = int(F & 7);
@@ -92,7 +93,8 @@ __device__ void interp_child(const TreeView &tv, const double *__restrict__ u, i
     }
 }
 
-__device__ __forceinline__ unsigned long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
 
 template <typename R, int D, int RS>
 struct Smem {
@@ -104,8 +106,63 @@ struct Smem {
     double dtmin[32];
 };
 
+// Riemann problem at face r0 of direction DIR: left state = predicted cell + half its
+// slope, right state = next cell - half its slope (floored), in the face-normal frame.
+template <typename R, int D, int RS, int DIR>
+__device__ __forceinline__ void face_flux(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>::NF], int r0, const Prm<R> &pr,
+                                          int32_t *status)
+{
+    using G = Geo<D>;
+    const int fa = r0 % (G::CI + 1), t1 = (r0 / (G::CI + 1)) % G::CI, t2 = r0 / ((G::CI + 1) * G::CI);
+    // predicted-cell coordinates (stencil - 1) of the left cell
+    const int Lx = DIR == 0 ? fa : 1 + t1;
+    const int Ly = DIR == 0 ? 1 + t1 : DIR == 1 ? fa : 1 + t2;
+    const int Lz = DIR == 2 ? fa : 1 + t2;
+    const int pl = Lx + G::P * (Ly + G::P * Lz);
+    const int pR = pl + (DIR == 0 ? 1 : DIR == 1 ? G::P : G::P * G::P);
+    constexpr int N0 = DIR + 1, T1 = DIR == 0 ? 2 : 1, T2 = DIR == 2 ? 2 : 3;   // normal, transverse
+    constexpr int S = NV + NV * DIR;                                             // slopes along DIR
+    R WL[NV], WR[NV];
+    WL[0] = sm.Q[0][pl] + R(0.5) * sm.Q[S + 0][pl];
+    WR[0] = sm.Q[0][pR] - R(0.5) * sm.Q[S + 0][pR];
+    WL[1] = sm.Q[N0][pl] + R(0.5) * sm.Q[S + N0][pl];
+    WR[1] = sm.Q[N0][pR] - R(0.5) * sm.Q[S + N0][pR];
+    WL[2] = sm.Q[T1][pl] + R(0.5) * sm.Q[S + T1][pl];
+    WR[2] = sm.Q[T1][pR] - R(0.5) * sm.Q[S + T1][pR];
+    WL[3] = sm.Q[T2][pl] + R(0.5) * sm.Q[S + T2][pl];
+    WR[3] = sm.Q[T2][pR] - R(0.5) * sm.Q[S + T2][pR];
+    WL[4] = sm.Q[4][pl] + R(0.5) * sm.Q[S + 4][pl];
+    WR[4] = sm.Q[4][pR] - R(0.5) * sm.Q[S + 4][pR];
+    WL[0] = rmax(WL[0], pr.rho_floor); WR[0] = rmax(WR[0], pr.rho_floor);
+    WL[4] = rmax(WL[4], pr.p_floor); WR[4] = rmax(WR[4], pr.p_floor);
+    R Fn[NV];
+    if (RS == AMR_RIEMANN_EXACT) {
+        R ps, us;
+        const R tol = sizeof(R) == 8 ? R(1e-14) : R(1e-6);
+        const int e = exact_star(WL, WR, pr.gamma, tol, 50, ps, us);
+        if (e == 0) {
+            R W0[NV], U0[NV];
+            exact_sample0(WL, WR, pr.gamma, ps, us, W0);
+            flux_normal(W0, pr.gamma, Fn, U0);
+        } else {
+            set_error(status, e);
+            hllc(WL, WR, pr.gamma, Fn);
+        }
+    } else {
+        hllc(WL, WR, pr.gamma, Fn);
+    }
+    sF[DIR][0][r0] = Fn[0];
+    sF[DIR][N0][r0] = Fn[1];
+    sF[DIR][T1][r0] = Fn[2];
+    sF[DIR][T2][r0] = Fn[3];
+    sF[DIR][4][r0] = Fn[4];
+}
+
+// threads per CTA: depth-1 tiles (512 stencil cells) 128, depth-2 tiles (1728) 512
+template <int D> constexpr int threads_for() { return D == 1 ? 128 : 512; }
+
 template <typename R, int D, int RS>
-__global__ void __launch_bounds__(128) k_godunov(GArgs a)
+__global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
 {
     using G = Geo<D>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -130,10 +187,11 @@ __global__ void __launch_bounds__(128) k_godunov(GArgs a)
         const double dx = ldexp(1.0, -l);
         const double lam = dt / dx;
         int mine_out = 0;
+        const bool finer = l < tv.levelmax;   // only then can a stencil cell be refined
         for (int s = tid; s < G::NSLOT; s += blockDim.x) {
             const int32_t e = a.tile_slot[t * G::NSLOT + s];
             sm.slot[s] = e;
-            sm.ref[s] = e >= 0 ? tv.refmask[e] : 0;
+            sm.ref[s] = (e >= 0 && finer) ? tv.refmask[e] : 0;
             mine_out |= (e == OUTSIDE);
         }
         const int any_outside = __syncthreads_or(mine_out);   // barrier: slots visible to all
@@ -181,7 +239,8 @@ __global__ void __launch_bounds__(128) k_godunov(GArgs a)
         }
 
         // ---- phase 2: slopes + predictor on stencil cells 1..C-2
-        const R hl = R(0.5 * lam);
+        const R lamR = to_work<R>(lam);
+        const R hl = R(0.5) * lamR;
         for (int p = tid; p < G::NP; p += blockDim.x) {
             const int i = 1 + p % G::P, j = 1 + (p / G::P) % G::P, k = 1 + p / (G::P * G::P);
             const int si = i + G::C * (j + G::C * k);
@@ -212,62 +271,28 @@ __global__ void __launch_bounds__(128) k_godunov(GArgs a)
 
         // ---- phase 3: Riemann problem at every face touching an updated cell
         for (int f = tid; f < 3 * G::NF; f += blockDim.x) {
-            const int d = f / G::NF, r0 = f % G::NF;
-            const int fa = r0 % (G::CI + 1), t1 = (r0 / (G::CI + 1)) % G::CI, t2 = r0 / ((G::CI + 1) * G::CI);
-            // predicted-cell coordinates (stencil - 1) of the left cell
-            int L[3];
-            if (d == 0) { L[0] = fa; L[1] = 1 + t1; L[2] = 1 + t2; }
-            else if (d == 1) { L[0] = 1 + t1; L[1] = fa; L[2] = 1 + t2; }
-            else { L[0] = 1 + t1; L[1] = 1 + t2; L[2] = fa; }
-            const int pl = L[0] + G::P * (L[1] + G::P * L[2]);
-            const int pR = pl + (d == 0 ? 1 : d == 1 ? G::P : G::P * G::P);
-            const int perm[3] = {d + 1, d == 0 ? 2 : 1, d == 2 ? 2 : 3};
-            R WL[NV], WR[NV];
-            WL[0] = sm.Q[0][pl] + R(0.5) * sm.Q[NV + NV * d][pl];
-            WR[0] = sm.Q[0][pR] - R(0.5) * sm.Q[NV + NV * d][pR];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                WL[1 + q] = sm.Q[perm[q]][pl] + R(0.5) * sm.Q[NV + NV * d + perm[q]][pl];
-                WR[1 + q] = sm.Q[perm[q]][pR] - R(0.5) * sm.Q[NV + NV * d + perm[q]][pR];
-            }
-            WL[4] = sm.Q[4][pl] + R(0.5) * sm.Q[NV + NV * d + 4][pl];
-            WR[4] = sm.Q[4][pR] - R(0.5) * sm.Q[NV + NV * d + 4][pR];
-            WL[0] = rmax(WL[0], pr.rho_floor); WR[0] = rmax(WR[0], pr.rho_floor);
-            WL[4] = rmax(WL[4], pr.p_floor); WR[4] = rmax(WR[4], pr.p_floor);
-            R Fn[NV];
-            if (RS == AMR_RIEMANN_EXACT) {
-                R ps, us;
-                const R tol = sizeof(R) == 8 ? R(1e-14) : R(1e-6);
-                const int e = exact_star(WL, WR, pr.gamma, tol, 50, ps, us);
-                if (e == 0) {
-                    R W0[NV], U0[NV];
-                    exact_sample0(WL, WR, pr.gamma, ps, us, W0);
-                    flux_normal(W0, pr.gamma, Fn, U0);
-                } else {
-                    set_error(a.status, e);
-                    hllc(WL, WR, pr.gamma, Fn);
-                }
-            } else {
-                hllc(WL, WR, pr.gamma, Fn);
-            }
-            sF[d][0][r0] = Fn[0];
-            sF[d][4][r0] = Fn[4];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) sF[d][perm[q]][r0] = Fn[1 + q];
+            const int d = f / G::NF, r0 = f - d * G::NF;
+            if (d == 0) face_flux<R, D, RS, 0>(sm, sF, r0, pr, a.status);
+            else if (d == 1) face_flux<R, D, RS, 1>(sm, sF, r0, pr, a.status);
+            else face_flux<R, D, RS, 2>(sm, sF, r0, pr, a.status);
         }
         __syncthreads();
 
         // ---- phase 4: FP64 update of existing cells + fused CFL candidate
-        double my_dt = DBL_MAX;
+        // new states of octs whose father is restricted here, in the (now free) predictor buffer
+        double(*sU)[G::NI] = reinterpret_cast<double(*)[G::NI]>(&sm.Q[0][0]);
+        static_assert(sizeof(double) * NV * G::NI <= sizeof(R) * 4 * NV * G::NP, "restriction buffer");
+        unsigned long long my_dt = ~0ull;   // bit pattern of the smallest positive candidate
         for (int q = tid; q < G::NI; q += blockDim.x) {
             const int c = q & 7, o = q >> 3;
             const int ox = 1 + o % G::OI, oy = 1 + (o / G::OI) % G::OI, oz = 1 + o / (G::OI * G::OI);
             const int s = ox + G::NS * (oy + G::NS * oz);
             const int32_t e = sm.slot[s];
             if (e < 0) continue;                                    // no oct here: nothing to update
+            if ((sm.ref[s] >> c) & 1) continue;   // refined: its value comes from the restriction
             const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
             const int ii[3] = {2 * ox + cx - 2, 2 * oy + cy - 2, 2 * oz + cz - 2};   // interior coords 0..CI-1
-            double dU[NV] = {0, 0, 0, 0, 0};
+            R dU[NV] = {0, 0, 0, 0, 0};     // flux sums in the working precision
             bool nbref = false;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -279,12 +304,12 @@ __global__ void __launch_bounds__(128) k_godunov(GArgs a)
                     nc[d] += side ? 1 : -1;
                     const int ns = (nc[0] >> 1) + G::NS * ((nc[1] >> 1) + G::NS * (nc[2] >> 1));
                     const int ncc = (nc[0] & 1) + 2 * (nc[1] & 1) + 4 * (nc[2] & 1);
-                    if (sm.slot[ns] >= 0 && ((sm.ref[ns] >> ncc) & 1)) { nbref = true; continue; }
+                    if (finer && sm.slot[ns] >= 0 && ((sm.ref[ns] >> ncc) & 1)) { nbref = true; continue; }
                     const int fa = ii[d] + side;
                     const int r0 = fa + (G::CI + 1) * (t1 + G::CI * t2);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        const double F = double(sF[d][v][r0]);
+                        const R F = sF[d][v][r0];
                         dU[v] = side ? dU[v] - F : dU[v] + F;
                     }
                 }
@@ -293,28 +318,40 @@ __global__ void __launch_bounds__(128) k_godunov(GArgs a)
             double Un[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                Un[v] = a.u_old[v * tv.ncell + cell] + lam * dU[v];
+                // FP64 accumulation: U_new = U_old + dt/dx * (sum of face fluxes); in the FP32 path
+                // the increment is formed in FP32 (dt/dx is exact there: dt is an FP32 value and
+                // dx a power of two) and added in FP64
+                if (sizeof(R) == 8) Un[v] = a.u_old[v * tv.ncell + cell] + lam * to_state(dU[v]);
+                else Un[v] = a.u_old[v * tv.ncell + cell] + to_state(lamR * dU[v]);
                 a.u_new[v * tv.ncell + cell] = Un[v];
             }
-            if (a.dt_next && !nbref && !((sm.ref[s] >> c) & 1)) {
+            if (tv.fused[e]) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sU[v][q] = Un[v];   // kept for the restriction pass
+            }
+            if (a.dt_next && !nbref) {
                 // CFL candidate (newdt_fine) from the final new state of this leaf cell
-                Prm<double> pd;
-                pd.gamma = a.gamma; pd.rho_floor = a.rho_floor; pd.p_floor = a.p_floor;
-                double Wn[NV];
-                cons_to_prim(Un, pd, Wn);
-                const double cs = sqrt(a.gamma * Wn[4] / Wn[0]);
-                const double sig = (fabs(Wn[1]) + cs) + (fabs(Wn[2]) + cs) + (fabs(Wn[3]) + cs);
-                const double cand = a.cfl * (dx / sig);
-                my_dt = cand < my_dt ? cand : my_dt;
+                const double cand = cfl_candidate<R>(Un, a.gamma, a.rho_floor, a.p_floor, a.cfl, dx);
+                my_dt = umin64(my_dt, dbits(cand));
             }
         }
         if (a.dt_next) {
-            for (int off = 16; off > 0; off >>= 1) {
-                const double o = __shfl_xor_sync(0xffffffffu, my_dt, off);
-                my_dt = o < my_dt ? o : my_dt;
-            }
-            if ((tid & 31) == 0 && my_dt < DBL_MAX)
-                atomicMin(reinterpret_cast<unsigned long long *>(a.dt_next), dbits(my_dt));
+            for (int off = 16; off > 0; off >>= 1) my_dt = umin64(my_dt, __shfl_xor_sync(0xffffffffu, my_dt, off));
+            if ((tid & 31) == 0 && my_dt != ~0ull) atomicMin(reinterpret_cast<unsigned long long *>(a.dt_next), my_dt);
+        }
+
+        // ---- restriction of father cells whose eight children are final here: one thread per
+        // (oct, variable), children summed in cell order, so every FP64 lane does useful work
+        __syncthreads();
+        for (int w = tid; w < G::OI * G::OI * G::OI * NV; w += blockDim.x) {
+            const int o = w / NV, v = w % NV;
+            const int ox = 1 + o % G::OI, oy = 1 + (o / G::OI) % G::OI, oz = 1 + o / (G::OI * G::OI);
+            const int32_t e = sm.slot[ox + G::NS * (oy + G::NS * oz)];
+            if (e < 0 || !tv.fused[e]) continue;
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc += sU[v][o * 8 + c];
+            a.u_new[v * tv.ncell + tv.father[e]] = 0.125 * acc;
         }
 
         // ---- flux register: oct sides whose neighbour slot is a coarse leaf
@@ -336,7 +373,7 @@ __global__ void __launch_bounds__(128) k_godunov(GArgs a)
                     const int t1 = ii[d == 0 ? 1 : 0], t2 = ii[d == 2 ? 1 : 2];
                     const int r0 = (ii[d] + side) + (G::CI + 1) * (t1 + G::CI * t2);
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) sum[v] += double(sF[d][v][r0]);
+                    for (int v = 0; v < NV; ++v) sum[v] += to_state(sF[d][v][r0]);
                 }
                 const int64_t row = (int64_t(e) - tv.reg_base) * 6 + f;
 #pragma unroll
@@ -355,27 +392,28 @@ static amr_status launch(const GArgs &a, int64_t ntile, cudaStream_t st)
     auto kern = k_godunov<R, D, RS>;
     AMR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
     const int64_t grid = ntile < 1048576 ? ntile : 1048576;
-    kern<<<unsigned(grid), 128, bytes, st>>>(a);
+    kern<<<unsigned(grid), threads_for<D>(), bytes, st>>>(a);
     AMR_CUDA_TRY(cudaGetLastError());
     return AMR_OK;
 }
 
-amr_status godunov_dispatch(const amr_tree *t, int level, const hydro_params *p, const double *u_old,
-                            double *u_new, double *reg, const double *dt, double *dt_next, cudaStream_t st)
+// Launch the kernel(s) of precision R for one level or for all levels (level = -1).
+// Levels whose tiles of the requested depth would be rooted above level 1 use depth 1.
+template <typename R>
+amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, const double *u_old, double *u_new,
+                         double *reg, const double *dt, double *dt_next, cudaStream_t st)
 {
-    int depth = p->tile == 0 ? 1 : p->tile;
+    const int depth = p->tile == 0 ? 1 : p->tile;
     if (depth != 1 && depth != 2) return AMR_EINVAL;
-    if (depth == 2 && p->precision == AMR_PREC_FP64) return AMR_EINVAL;   // FP64 stencil of 12^3 cells exceeds smem
+    if (depth == 2 && sizeof(R) == 8) return AMR_EINVAL;   // an FP64 12^3-cell stencil does not fit in smem
     const int l0 = level < 0 ? t->levelmin : level, l1 = level < 0 ? t->levelmax : level;
     if (l0 < t->levelmin || l1 > t->levelmax) return AMR_EINVAL;
-    // levels that cannot form tiles of this depth (root above level 1) use depth 1
     int lsplit = l0;
     while (lsplit <= l1 && lsplit - depth < 1) ++lsplit;
     for (int pass = 0; pass < 2; ++pass) {
         const int d = pass == 0 ? 1 : depth;
         const int la = pass == 0 ? l0 : lsplit, lb = pass == 0 ? lsplit - 1 : l1;
-        if (pass == 0 && depth == 1) continue;
-        if (la > lb) continue;
+        if ((pass == 0 && depth == 1) || la > lb) continue;
         GArgs a;
         a.tv = make_view(t);
         a.tile_root = t->tile_root[d - 1];
@@ -389,15 +427,10 @@ amr_status godunov_dispatch(const amr_tree *t, int level, const hydro_params *p,
         a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
         a.status = p->d_status; a.counters = p->d_counters;
         const int64_t nt = a.t_end - a.t_begin;
-        amr_status r = AMR_OK;
-        const bool fp32 = p->precision == AMR_PREC_FP32;
         const bool ex = p->riemann == AMR_RIEMANN_EXACT;
-        if (d == 1) {
-            if (fp32) r = ex ? launch<float, 1, 1>(a, nt, st) : launch<float, 1, 0>(a, nt, st);
-            else r = ex ? launch<double, 1, 1>(a, nt, st) : launch<double, 1, 0>(a, nt, st);
-        } else {
-            r = ex ? launch<float, 2, 1>(a, nt, st) : launch<float, 2, 0>(a, nt, st);
-        }
+        amr_status r;
+        if (d == 1) r = ex ? launch<R, 1, 1>(a, nt, st) : launch<R, 1, 0>(a, nt, st);
+        else r = ex ? launch<R, 2 - (sizeof(R) == 8), 1>(a, nt, st) : launch<R, 2 - (sizeof(R) == 8), 0>(a, nt, st);
         if (r != AMR_OK) return r;
     }
     return AMR_OK;

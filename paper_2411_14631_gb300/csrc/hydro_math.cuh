@@ -8,14 +8,47 @@
 
 namespace amr {
 
+// FP64 <-> FP32 by integer bit manipulation.  On sm_103a the hardware conversions run on
+// the FP64 pipe (about 2 per clock per SM), as slow as FP64 arithmetic; these run on the
+// integer ALUs.  d2f: round to nearest on the dropped bits (ties away from zero); values
+// below the FP32 normal range become zero; |x| must be below 2^128.  f2d: exact for
+// normal floats, zero for zero and FP32 denormals.
+__device__ __forceinline__ float d2f_bits(double x)
+{
+    const unsigned hi = unsigned(__double2hiint(x)), lo = unsigned(__double2loint(x));
+    const unsigned ahi = hi & 0x7FFFFFFFu;
+    unsigned m = __funnelshift_l(lo, ahi, 3) - (896u << 23);   // rebias 1023 -> 127, keep 23 mantissa bits
+    m += (lo >> 28) & 1u;
+    m = ahi < (897u << 20) ? 0u : m;
+    return __uint_as_float(m | (hi & 0x80000000u));
+}
+
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const unsigned b = __float_as_uint(f), ab = b & 0x7FFFFFFFu;
+    const bool z = ab < 0x00800000u;
+    const unsigned hi = z ? 0u : (ab >> 3) + (896u << 20);
+    const unsigned lo = z ? 0u : ab << 29;
+    return __hiloint2double(int(hi | (b & 0x80000000u)), int(lo));
+}
+
+// working-precision view of an FP64 state value, and back
+template <typename R> __device__ __forceinline__ R to_work(double x);
+template <> __device__ __forceinline__ double to_work<double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_work<float>(double x) { return d2f_bits(x); }
+__device__ __forceinline__ double to_state(double x) { return x; }
+__device__ __forceinline__ double to_state(float x) { return f2d_bits(x); }
+
 template <typename R> struct Prm {
     R gamma, rho_floor, p_floor;
 };
 
+// MinMod: zero when the differences disagree in sign, else the smaller magnitude (equal
+// signs make copysign(min(|a|,|b|), a) the same value as the textbook branch)
 template <typename R> __device__ __forceinline__ R minmod(R a, R b)
 {
-    if (a * b <= R(0)) return R(0);
-    return fabs(a) < fabs(b) ? a : b;
+    const R m = copysign(fmin(fabs(a), fabs(b)), a);
+    return a * b > R(0) ? m : R(0);
 }
 
 template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
@@ -24,10 +57,10 @@ template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b
 template <typename R>
 __device__ __forceinline__ void cons_to_prim(const double U[NV], const Prm<R> &p, R W[NV])
 {
-    const R rho = rmax(R(U[0]), p.rho_floor);
-    const R u = R(U[1]) / rho, v = R(U[2]) / rho, w = R(U[3]) / rho;
+    const R rho = rmax(to_work<R>(U[0]), p.rho_floor);
+    const R u = to_work<R>(U[1]) / rho, v = to_work<R>(U[2]) / rho, w = to_work<R>(U[3]) / rho;
     const R ek = R(0.5) * rho * (u * u + v * v + w * w);
-    const R pr = (p.gamma - R(1)) * (R(U[4]) - ek);
+    const R pr = (p.gamma - R(1)) * (to_work<R>(U[4]) - ek);
     W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
     W[4] = rmax(pr, p.p_floor);
 }
@@ -47,7 +80,7 @@ __device__ __forceinline__ void flux_normal(const R W[NV], R g, R F[NV], R U[NV]
 }
 
 // HLLC flux (Toro, Spruce & Speares 1994); the side used is chosen before computing,
-// so every face does one star state (no divergent branches).
+// so every face does one star state (no divergent branches, no register-array pointers).
 template <typename R>
 __device__ __forceinline__ void hllc(const R WL[NV], const R WR[NV], R g, R F[NV])
 {
@@ -59,7 +92,9 @@ __device__ __forceinline__ void hllc(const R WL[NV], const R WR[NV], R g, R F[NV
     const R Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR));
     const bool left = (SL >= R(0)) || (Ss >= R(0));
     const bool star = !(SL >= R(0)) && (Ss >= R(0) || SR > R(0));
-    const R *WK = left ? WL : WR;
+    R WK[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) WK[v] = left ? WL[v] : WR[v];
     const R SK = left ? SL : SR;
     R FK[NV], UK[NV];
     flux_normal(WK, g, FK, UK);
@@ -135,10 +170,9 @@ __device__ void exact_sample0(const R WL[NV], const R WR[NV], R g, R ps, R us, R
     const R g5 = R(2) / (g + R(1)), g6 = (g - R(1)) / (g + R(1)), g7 = (g - R(1)) / R(2);
     const R S = R(0);
     R rho, u, p;
-    const R *T;
-    if (S <= us) {
+    const bool lside = S <= us;
+    if (lside) {
         const R rL = WL[0], uL = WL[1], pL = WL[4], cL = sqrt(g * pL / rL);
-        T = WL;
         if (ps > pL) {
             const R SL = uL - cL * sqrt(g2 * ps / pL + g1);
             if (S <= SL) { rho = rL; u = uL; p = pL; }
@@ -160,7 +194,6 @@ __device__ void exact_sample0(const R WL[NV], const R WR[NV], R g, R ps, R us, R
         }
     } else {
         const R rR = WR[0], uR = WR[1], pR = WR[4], cR = sqrt(g * pR / rR);
-        T = WR;
         if (ps > pR) {
             const R SR = uR + cR * sqrt(g2 * ps / pR + g1);
             if (S >= SR) { rho = rR; u = uR; p = pR; }
@@ -181,7 +214,25 @@ __device__ void exact_sample0(const R WL[NV], const R WR[NV], R g, R ps, R us, R
             }
         }
     }
-    W[0] = rho; W[1] = u; W[2] = T[2]; W[3] = T[3]; W[4] = p;
+    W[0] = rho; W[1] = u; W[2] = lside ? WL[2] : WR[2]; W[3] = lside ? WL[3] : WR[3]; W[4] = p;
+}
+
+// dt candidate of one cell: cfl * dx / sum_d (|u_d| + c)
+template <typename R>
+__device__ __forceinline__ double cfl_candidate(const double U[NV], double gamma, double rf, double pf, double cfl,
+                                                double dx)
+{
+    Prm<R> p;
+    p.gamma = R(gamma); p.rho_floor = R(rf); p.p_floor = R(pf);
+    R W[NV];
+    cons_to_prim(U, p, W);
+    const R cs = sqrt(p.gamma * W[4] / W[0]);
+    const R sig = (fabs(W[1]) + cs) + (fabs(W[2]) + cs) + (fabs(W[3]) + cs);
+    if (sizeof(R) == 8) return cfl * (dx / double(sig));
+    // FP32: scaled down by (1 - 2^-16) so it never exceeds the FP64 value; dx is a power
+    // of two, cfl is converted once per call site by the compiler's constant folding
+    const float c32 = d2f_bits(cfl) * (d2f_bits(dx) / float(sig));
+    return f2d_bits(c32 * 0.9999847412109375f);
 }
 
 }  // namespace amr

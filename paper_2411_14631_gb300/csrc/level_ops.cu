@@ -5,34 +5,20 @@
 #include "hydro_math.cuh"
 
 namespace amr {
-amr_status godunov_dispatch(const amr_tree *t, int level, const hydro_params *p, const double *u_old,
-                            double *u_new, double *reg, const double *dt, double *dt_next, cudaStream_t st);
+amr_status godunov_dispatch_fp32(const amr_tree *t, int level, const hydro_params *p, const double *u_old,
+                                 double *u_new, double *reg, const double *dt, double *dt_next, cudaStream_t st);
+amr_status godunov_dispatch_fp64(const amr_tree *t, int level, const hydro_params *p, const double *u_old,
+                                 double *u_new, double *reg, const double *dt, double *dt_next, cudaStream_t st);
 
+// warp minimum of positive doubles (compared as their bit patterns), then one atomic per warp
 __device__ __forceinline__ void min_to(double *target, double v)
 {
+    unsigned long long b = v < DBL_MAX ? (unsigned long long)__double_as_longlong(v) : ~0ull;
     for (int off = 16; off > 0; off >>= 1) {
-        const double o = __shfl_xor_sync(0xffffffffu, v, off);
-        v = o < v ? o : v;
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, b, off);
+        b = o < b ? o : b;
     }
-    if ((threadIdx.x & 31) == 0 && v < DBL_MAX)
-        atomicMin(reinterpret_cast<unsigned long long *>(target), (unsigned long long)__double_as_longlong(v));
-}
-
-// dt candidate of one cell: cfl * dx / sum_d (|u_d| + c)
-template <typename R>
-__device__ __forceinline__ double cfl_candidate(const double U[NV], double gamma, double rf, double pf, double cfl,
-                                                double dx)
-{
-    Prm<R> p;
-    p.gamma = R(gamma); p.rho_floor = R(rf); p.p_floor = R(pf);
-    R W[NV];
-    cons_to_prim(U, p, W);
-    const R cs = sqrt(p.gamma * W[4] / W[0]);
-    const R sig = (fabs(W[1]) + cs) + (fabs(W[2]) + cs) + (fabs(W[3]) + cs);
-    if (sizeof(R) == 8) return cfl * (dx / double(sig));
-    // FP32: scaled down by (1 - 2^-16) so it never exceeds the FP64 value
-    const float c32 = float(cfl) * (float(dx) / float(sig));
-    return double(c32 * 0.9999847412109375f);
+    if ((threadIdx.x & 31) == 0 && b != ~0ull) atomicMin(reinterpret_cast<unsigned long long *>(target), b);
 }
 
 template <typename R>
@@ -55,7 +41,7 @@ __global__ void k_courant(TreeView tv, int64_t cell0, const double *__restrict__
 // mean of their eight children.
 template <typename R>
 __global__ void k_reflux(TreeView tv, int level, const double *__restrict__ reg, double *u, const double *dtp,
-                         double *dt_next, double gamma, double rf, double pf, double cfl)
+                         double *dt_next, double gamma, double rf, double pf, double cfl, int restrict_all)
 {
     const int64_t cell = tv.lvl_off[level] * 8 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     double cand = DBL_MAX;
@@ -64,12 +50,14 @@ __global__ void k_reflux(TreeView tv, int level, const double *__restrict__ reg,
         const int c = int(cell & 7);
         const int32_t s = tv.son[cell];
         if (s >= 0) {
+            if (restrict_all || !tv.fused[s]) {               // else restricted by the update kernel
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                double sum = 0.0;
+                for (int v = 0; v < NV; ++v) {
+                    double sum = 0.0;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) sum += u[v * tv.ncell + int64_t(s) * 8 + q];
-                u[v * tv.ncell + cell] = 0.125 * sum;
+                    for (int q = 0; q < 8; ++q) sum += u[v * tv.ncell + int64_t(s) * 8 + q];
+                    u[v * tv.ncell + cell] = 0.125 * sum;
+                }
             }
         } else if (reg && level >= tv.levelmin) {
             const double lam = *dtp / ldexp(1.0, -level);
@@ -147,16 +135,18 @@ static amr_status check(const amr_tree *t, const hydro_params *p)
 }
 
 static amr_status reflux_launch(const amr_tree *t, int level, const hydro_params *p, const double *reg, double *u,
-                                const double *dt, double *dt_next, cudaStream_t st)
+                                const double *dt, double *dt_next, cudaStream_t st, int restrict_all = 0)
 {
     const int64_t nc = (t->lvl_off[level + 1] - t->lvl_off[level]) * 8;
     if (nc <= 0) return AMR_OK;
     const unsigned nb = unsigned((nc + 255) / 256);
     const TreeView tv = make_view(t);
     if (p->precision == AMR_PREC_FP32)
-        k_reflux<float><<<nb, 256, 0, st>>>(tv, level, reg, u, dt, dt_next, p->gamma, p->rho_floor, p->p_floor, p->cfl);
+        k_reflux<float><<<nb, 256, 0, st>>>(tv, level, reg, u, dt, dt_next, p->gamma, p->rho_floor, p->p_floor, p->cfl,
+                                            restrict_all);
     else
-        k_reflux<double><<<nb, 256, 0, st>>>(tv, level, reg, u, dt, dt_next, p->gamma, p->rho_floor, p->p_floor, p->cfl);
+        k_reflux<double><<<nb, 256, 0, st>>>(tv, level, reg, u, dt, dt_next, p->gamma, p->rho_floor, p->p_floor, p->cfl,
+                                             restrict_all);
     AMR_CUDA_TRY(cudaGetLastError());
     return AMR_OK;
 }
@@ -181,7 +171,7 @@ extern "C" amr_status hydro_init_from_prim(const amr_tree *t, const hydro_params
     k_prim_to_cons<<<unsigned((nc + 255) / 256), 256, 0, st>>>(nc, d_w, d_u, p->gamma);
     AMR_CUDA_TRY(cudaGetLastError());
     for (int l = t->levelmax - 1; l >= 1; --l) {
-        amr_status r = reflux_launch(t, l, p, nullptr, d_u, nullptr, nullptr, st);
+        amr_status r = reflux_launch(t, l, p, nullptr, d_u, nullptr, nullptr, st, 1);
         if (r != AMR_OK) return r;
     }
     return AMR_OK;
@@ -223,8 +213,10 @@ extern "C" amr_status hydro_godunov_level(const amr_tree *t, int level, const hy
     if (p->riemann == AMR_RIEMANN_MLP) return AMR_EINVAL;   // the surrogate runs through its own entry points
     if (level != -1 && (level < t->levelmin || level > t->levelmax)) return AMR_EINVAL;
     if (t->levelmax > t->levelmin && !d_flux_reg) return AMR_EINVAL;
-    return godunov_dispatch(t, level, p, d_u_old, d_u_new, d_flux_reg, d_dt, d_dt_next,
-                            reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (p->precision == AMR_PREC_FP32)
+        return godunov_dispatch_fp32(t, level, p, d_u_old, d_u_new, d_flux_reg, d_dt, d_dt_next, st);
+    return godunov_dispatch_fp64(t, level, p, d_u_old, d_u_new, d_flux_reg, d_dt, d_dt_next, st);
 }
 
 extern "C" amr_status hydro_reflux_level(const amr_tree *t, int level, const hydro_params *p, const double *d_flux_reg,

@@ -15,7 +15,7 @@ constexpr int32_t UNNEEDED = INT32_MIN + 1;
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct TreeLayout {
-    size_t lvl, ix, iy, iz, key, son, father, nbor, nb27, refmask, root[2], slot[2], total;
+    size_t lvl, ix, iy, iz, key, son, father, nbor, nb27, refmask, fused, root[2], slot[2], total;
     int64_t tile_bound[2];
 };
 
@@ -36,7 +36,7 @@ static TreeLayout tree_layout(int64_t n, const int64_t cnt[AMR_MAXLEV + 2], int 
     auto put = [&](size_t bytes) { size_t at = o; o += al256(bytes); return at; };
     L.lvl = put(4 * n); L.ix = put(4 * n); L.iy = put(4 * n); L.iz = put(4 * n);
     L.key = put(8 * n); L.son = put(32 * n); L.father = put(4 * n); L.nbor = put(24 * n);
-    L.nb27 = put(108 * n); L.refmask = put(n);
+    L.nb27 = put(108 * n); L.refmask = put(n); L.fused = put(n);
     for (int d = 0; d < 2; ++d) {
         L.root[d] = put(4 * L.tile_bound[d]);
         L.slot[d] = put(4 * L.tile_bound[d] * nslot(d + 1));
@@ -189,6 +189,28 @@ __global__ void k_tables(BuildView b, int32_t *son, int32_t *father, int32_t *nb
     }
 }
 
+// An oct whose eight cells are leaves and have no refined same-level face neighbour:
+// its cells are final after the Godunov update (no reflux, no restriction reaches them),
+// so the update kernel can also restrict its father cell.
+__global__ void k_fused(BuildView b, const int32_t *__restrict__ son, const int32_t *__restrict__ nbor,
+                        const uint8_t *__restrict__ refmask, uint8_t *fused)
+{
+    const int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (o >= b.n) return;
+    uint8_t ok = b.lvl[o] >= 2 && refmask[o] == 0;
+    for (int f = 0; f < 6 && ok; ++f) {
+        const int32_t N = nbor[6 * o + f];
+        if (N < 0) continue;
+        const int32_t so = son[N];
+        if (so < 0) continue;
+        const int d = f >> 1, side = f & 1;
+        // cells of the neighbour oct facing this oct sit at position 1 - side along d
+        for (int c = 0; c < 8; ++c)
+            if (((c >> d) & 1) == 1 - side && ((refmask[so] >> c) & 1)) ok = 0;
+    }
+    fused[o] = ok;
+}
+
 // flag octs that root a tile of the given depth: a descendant `depth` levels down
 __global__ void k_tile_flags(BuildView b, const int32_t *__restrict__ son, const uint8_t *__restrict__ refmask,
                              int depth, int32_t *flag)
@@ -307,6 +329,7 @@ extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oc
     out->iz = (int32_t *)(T + L.iz); out->key = (uint64_t *)(T + L.key); out->son = (int32_t *)(T + L.son);
     out->father = (int32_t *)(T + L.father); out->nbor = (int32_t *)(T + L.nbor);
     out->nb27 = (int32_t *)(T + L.nb27); out->refmask = (uint8_t *)(T + L.refmask);
+    out->fused = (uint8_t *)(T + L.fused);
     for (int d = 0; d < 2; ++d) {
         out->tile_root[d] = (int32_t *)(T + L.root[d]);
         out->tile_slot[d] = (int32_t *)(T + L.slot[d]);
@@ -334,6 +357,7 @@ extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oc
     for (int l = 0; l < AMR_MAXLEV + 2; ++l) bv.lvl_off[l] = out->lvl_off[l];
     bv.lvl = out->lvl; bv.ix = out->ix; bv.iy = out->iy; bv.iz = out->iz; bv.key = out->key;
     k_tables<<<nb, TB, 0, st>>>(bv, out->son, out->father, out->nbor, out->nb27, out->refmask, err);
+    k_fused<<<nb, TB, 0, st>>>(bv, out->son, out->nbor, out->refmask, out->fused);
 
     for (int d = 0; d < 2; ++d) {
         const int depth = d + 1;

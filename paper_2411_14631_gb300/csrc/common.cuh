@@ -1,6 +1,7 @@
 // Internal device helpers shared by the amrhydro kernels (sm_103a).
 #pragma once
 #include <cstdint>
+#include <cmath>
 #include <cuda_runtime.h>
 #include "../../include/amrhydro.h"
 
@@ -53,6 +54,21 @@ __host__ __device__ inline uint64_t hilbert3(int bits, uint32_t x, uint32_t y, u
         for (int i = 0; i < 3; ++i) key = (key << 1) | (((a[i] ^ flip) >> b) & 1u);
     }
     return key;
+}
+
+// 2^e and x * 2^e (x > 0 and normal) by exponent arithmetic on the bit pattern: exact,
+// and off the FP64 pipe
+__host__ __device__ inline double pow2(int e)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)(1023 + e) << 52);
+#else
+    return ldexp(1.0, e);
+#endif
+}
+__device__ __forceinline__ double scale_pow2(double x, int e)
+{
+    return __longlong_as_double(__double_as_longlong(x) + ((long long)e << 52));
 }
 
 // Oct index of (l, x, y, z) in the level-sorted key array, or -1.

@@ -173,7 +173,8 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
     const int tid = threadIdx.x;
     const double dt = *a.dt;
     Prm<R> pr;
-    pr.gamma = R(a.gamma); pr.rho_floor = R(a.rho_floor); pr.p_floor = R(a.p_floor);
+    pr.gamma = to_work<R>(a.gamma); pr.rho_floor = to_work<R>(a.rho_floor); pr.p_floor = to_work<R>(a.p_floor);
+    const R cflR = to_work<R>(a.cfl);
 
     for (int64_t t = a.t_begin + blockIdx.x; t < a.t_end; t += gridDim.x) {
         // ---- level of this tile and its geometry
@@ -184,8 +185,8 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
         // a depth-D root covers 2^(D+1) level-l cells per axis; stencil index 0 is two cells before
         const int64_t X0[3] = {int64_t(tv.ix[root]) * (2 << D) - 2, int64_t(tv.iy[root]) * (2 << D) - 2,
                                int64_t(tv.iz[root]) * (2 << D) - 2};
-        const double dx = ldexp(1.0, -l);
-        const double lam = dt / dx;
+        const double dx = pow2(-l);
+        const double lam = scale_pow2(dt, l);    // dt / dx, exact
         int mine_out = 0;
         const bool finer = l < tv.levelmax;   // only then can a stencil cell be refined
         for (int s = tid; s < G::NSLOT; s += blockDim.x) {
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
             }
             if (a.dt_next && !nbref) {
                 // CFL candidate (newdt_fine) from the final new state of this leaf cell
-                const double cand = cfl_candidate<R>(Un, a.gamma, a.rho_floor, a.p_floor, a.cfl, dx);
+                const double cand = cfl_candidate<R>(Un, pr, cflR, to_work<R>(dx));
                 my_dt = umin64(my_dt, dbits(cand));
             }
         }

@@ -217,22 +217,18 @@ __device__ void exact_sample0(const R WL[NV], const R WR[NV], R g, R ps, R us, R
     W[0] = rho; W[1] = u; W[2] = lside ? WL[2] : WR[2]; W[3] = lside ? WL[3] : WR[3]; W[4] = p;
 }
 
-// dt candidate of one cell: cfl * dx / sum_d (|u_d| + c)
+// dt candidate of one cell: cfl * dx / sum_d (|u_d| + c), from the FP64 state; p, cfl and
+// dx already in the working precision
 template <typename R>
-__device__ __forceinline__ double cfl_candidate(const double U[NV], double gamma, double rf, double pf, double cfl,
-                                                double dx)
+__device__ __forceinline__ double cfl_candidate(const double U[NV], const Prm<R> &p, R cfl, R dx)
 {
-    Prm<R> p;
-    p.gamma = R(gamma); p.rho_floor = R(rf); p.p_floor = R(pf);
     R W[NV];
     cons_to_prim(U, p, W);
     const R cs = sqrt(p.gamma * W[4] / W[0]);
     const R sig = (fabs(W[1]) + cs) + (fabs(W[2]) + cs) + (fabs(W[3]) + cs);
-    if (sizeof(R) == 8) return cfl * (dx / double(sig));
-    // FP32: scaled down by (1 - 2^-16) so it never exceeds the FP64 value; dx is a power
-    // of two, cfl is converted once per call site by the compiler's constant folding
-    const float c32 = d2f_bits(cfl) * (d2f_bits(dx) / float(sig));
-    return f2d_bits(c32 * 0.9999847412109375f);
+    if (sizeof(R) == 8) return double(cfl) * (double(dx) / double(sig));
+    // FP32: scaled down by (1 - 2^-16) so that it never exceeds the FP64 value
+    return to_state(float(cfl) * (float(dx) / float(sig)) * 0.9999847412109375f);
 }
 
 }  // namespace amr

@@ -31,7 +31,9 @@ __global__ void k_courant(TreeView tv, int64_t cell0, const double *__restrict__
         double U[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) U[v] = u[v * tv.ncell + cell];
-        cand = cfl_candidate<R>(U, gamma, rf, pf, cfl, ldexp(1.0, -tv.lvl[cell >> 3]));
+        Prm<R> p;
+        p.gamma = to_work<R>(gamma); p.rho_floor = to_work<R>(rf); p.p_floor = to_work<R>(pf);
+        cand = cfl_candidate<R>(U, p, to_work<R>(cfl), to_work<R>(pow2(-tv.lvl[cell >> 3])));
     }
     min_to(dt, cand);
 }
@@ -60,7 +62,7 @@ __global__ void k_reflux(TreeView tv, int level, const double *__restrict__ reg,
                 }
             }
         } else if (reg && level >= tv.levelmin) {
-            const double lam = *dtp / ldexp(1.0, -level);
+            const double lam = scale_pow2(*dtp, level);   // dt / dx, exact
             double U[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) U[v] = u[v * tv.ncell + cell];
@@ -91,7 +93,11 @@ __global__ void k_reflux(TreeView tv, int level, const double *__restrict__ reg,
             if (hit) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) u[v * tv.ncell + cell] = U[v];
-                if (dt_next) cand = cfl_candidate<R>(U, gamma, rf, pf, cfl, ldexp(1.0, -level));
+                if (dt_next) {
+                    Prm<R> p;
+                    p.gamma = to_work<R>(gamma); p.rho_floor = to_work<R>(rf); p.p_floor = to_work<R>(pf);
+                    cand = cfl_candidate<R>(U, p, to_work<R>(cfl), to_work<R>(pow2(-level)));
+                }
             }
         }
     }

@@ -170,6 +170,24 @@ amr_status hydro_step(const amr_tree *tree, const hydro_params *params, const do
                       double *d_u_new, double *d_flux_reg, const double *d_dt, double *d_dt_next,
                       amr_stream stream);
 
+/* hydro_step without any caller-provided scratch.  The paper has no counterpart: this
+   is an interface convenience.  Some callers cannot allocate device memory when they
+   want to step: code that records the step inside CUDA stream capture (cudaMalloc is
+   not a capturable operation), real-time loops that forbid allocation after start-up,
+   and hosts whose device memory is owned by another framework's memory pool.  For them,
+   the flux register lives in a fixed array inside this library, sized for at most
+   AMR_STATIC_REG_MAX_OCTS octs above levelmin (31.5 MB, held by every GPU that loads
+   the library until the process exits).  Trees with more such octs get AMR_ECAPACITY and
+   nothing runs.  Inputs and outputs are the caller's, as for hydro_step.  The first
+   call on each device looks up the array's device address (no allocation); make that
+   first call before any stream capture.  Every call shares the one array: calls whose
+   work overlaps on the GPU (other streams, other host threads) race and give wrong
+   results.  No register row needs a starting value: every row read in a call is written
+   earlier in the same call. */
+#define AMR_STATIC_REG_MAX_OCTS 131072
+amr_status hydro_step_static_scratch(const amr_tree *tree, const hydro_params *params, const double *d_u_old,
+                                     double *d_u_new, const double *d_dt, double *d_dt_next, amr_stream stream);
+
 /* Copy params->d_status and params->d_counters to the host (synchronises the device). */
 amr_status amr_get_status(const hydro_params *params, int32_t *h_status, unsigned long long *h_counters);
 

@@ -17,7 +17,8 @@ PREC_FP64, PREC_FP32 = 0, 1
 
 EXPORTS = ["amr_build_octree_query", "amr_build_octree", "hydro_init_from_prim", "hydro_prim_of_state",
            "hydro_courant", "hydro_godunov_level", "hydro_flux_reg_bytes", "hydro_reflux_level", "hydro_step",
-           "amr_get_status", "amr_status_string"]
+           "amr_get_status", "amr_status_string", "hydro_step_static_scratch"]
+STATIC_REG_MAX_OCTS = 131072
 
 
 class AmrGeom(C.Structure):
@@ -66,6 +67,7 @@ def lib():
     L.hydro_flux_reg_bytes.restype = S
     L.hydro_reflux_level.argtypes = [PT, C.c_int, PP, P, P, P, P, P]
     L.hydro_step.argtypes = [PT, PP, P, P, P, P, P, P]
+    L.hydro_step_static_scratch.argtypes = [PT, PP, P, P, P, P, P]
     L.amr_get_status.argtypes = [PP, P, P]
     L.amr_status_string.argtypes = [C.c_int]
     L.amr_status_string.restype = C.c_char_p

@@ -247,6 +247,31 @@ extern "C" amr_status hydro_step(const amr_tree *t, const hydro_params *p, const
     return AMR_OK;
 }
 
+// ---- hydro_step with the flux register in library-owned device memory ----------------
+// For callers that cannot allocate device memory when they step.  The register is a
+// fixed file-scope device array; host code must not pass the symbol itself to a kernel
+// (in host code it names a host-side stand-in), so its device address is looked up once
+// per device and cached.
+static __device__ __align__(256) double g_static_reg[size_t(AMR_STATIC_REG_MAX_OCTS) * 6 * NV];
+static double *g_static_reg_addr[256];
+
+extern "C" amr_status hydro_step_static_scratch(const amr_tree *t, const hydro_params *p, const double *d_u_old,
+                                                double *d_u_new, const double *d_dt, double *d_dt_next,
+                                                amr_stream stream)
+{
+    if (check(t, p) != AMR_OK || !d_u_old || !d_u_new || !d_dt) return AMR_EINVAL;
+    if (t->noct - t->reg_base > AMR_STATIC_REG_MAX_OCTS) return AMR_ECAPACITY;
+    int dev = 0;
+    AMR_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return AMR_EINVAL;
+    if (!g_static_reg_addr[dev]) {
+        void *addr = nullptr;
+        AMR_CUDA_TRY(cudaGetSymbolAddress(&addr, g_static_reg));
+        g_static_reg_addr[dev] = static_cast<double *>(addr);
+    }
+    return hydro_step(t, p, d_u_old, d_u_new, g_static_reg_addr[dev], d_dt, d_dt_next, stream);
+}
+
 extern "C" amr_status amr_get_status(const hydro_params *p, int32_t *h_status, unsigned long long *h_counters)
 {
     if (!p) return AMR_EINVAL;

@@ -118,6 +118,14 @@ def hydro_step(tree, prm, u_old, u_new, reg, dt, dt_next=None, stream=None):
                                          _ptr(dt), _ptr(dt_next), _stream(stream)))
 
 
+def hydro_step_static_scratch(tree, prm, u_old, u_new, dt, dt_next=None, stream=None):
+    """hydro_step with the flux register inside the library (for callers that cannot
+    allocate device memory when they step); see include/amrhydro.h."""
+    check("hydro_step_static_scratch",
+          lib().hydro_step_static_scratch(C.byref(tree.t), C.byref(prm.c), _ptr(u_old), _ptr(u_new), _ptr(dt),
+                                          _ptr(dt_next), _stream(stream)))
+
+
 class Simulation:
     """State buffers and the step sequence of one run (u_old -> u_new, dt on the device).
 

@@ -188,6 +188,57 @@ amr_status hydro_step(const amr_tree *tree, const hydro_params *params, const do
 amr_status hydro_step_static_scratch(const amr_tree *tree, const hydro_params *params, const double *d_u_old,
                                      double *d_u_new, const double *d_dt, double *d_dt_next, amr_stream stream);
 
+/* ---- learned Riemann surrogate --------------------------------------------------------
+   The paper has no learned component.  The project puts a small network in place of the
+   iterative exact Riemann solver (Toro 2009, Ch. 4) of godunov_fine (Table 1): 7 -> 64 ->
+   64 -> 64 -> 2, SiLU, BF16 weights with FP32 accumulation on the tensor cores.  Inputs
+   are the normalised face-normal problem (rho_ref = rho_L, p_ref = max(p_L,p_R),
+   c_ref = sqrt(p_ref/rho_ref), ubar = (u_L+u_R)/2):
+     x = [log(rho_L/rho_ref), (u_L-ubar)/c_ref, log(p_L/p_ref), log(rho_R/rho_ref),
+          (u_R-ubar)/c_ref, log(p_R/p_ref), gamma]  (stored as 8 floats, slot 7 unused),
+     y = [log(p_star/p_ref), (u_star-ubar)/c_ref].
+   Master parameters theta are FP32 in the order W1[64][7] b1 W2[64][64] b2 W3[64][64] b3
+   W4[2][64] b4 (AMR_MLP_NPARAMS values).  With params->riemann = AMR_RIEMANN_MLP
+   (AMR_PREC_FP32 only) the Godunov kernel evaluates the network at every face, accepts
+   (p_star, u_star) when p_star > 0 and both |f(p_star)| and the velocity relation are
+   within mlp_resid_tol * (c_L + c_R), and otherwise solves the face exactly; counters[0]
+   and [1] count accepted faces and fallbacks. */
+#define AMR_MLP_NPARAMS 8962
+int mlp_nparams(void);
+/* Bytes of the packed BF16 weight block (device, 16-byte aligned) used by every kernel. */
+size_t mlp_packed_bytes(void);
+/* Scratch bytes mlp_grad / mlp_train_step need for a batch of n samples. */
+size_t mlp_scratch_bytes(int64_t n);
+/* FP32 master parameters -> packed BF16 block. */
+amr_status mlp_pack(const float *d_theta, void *d_packed, amr_stream stream);
+/* Dataset from face states d_states[n][6] = (rho_L,u_L,p_L,rho_R,u_R,p_R) (FP64): the
+   exact FP64 solution labels each problem; writes d_x[n][8], d_y[n][2].  A problem the
+   exact solver rejects (vacuum, no convergence) sets *d_status (if not NULL). */
+amr_status mlp_make_dataset(const double *d_states, int64_t n, double gamma, float *d_x, float *d_y,
+                            int32_t *d_status, amr_stream stream);
+/* Inference: d_y[n][2] = net(d_x[n][8]). */
+amr_status mlp_forward(const void *d_packed, const float *d_x, float *d_y, int64_t n, amr_stream stream);
+/* d_grad[AMR_MLP_NPARAMS] = gradient of sum_i d_dy[i] . y(x_i) with respect to theta,
+   through the BF16 network (for gradient checks). */
+amr_status mlp_grad(const void *d_packed, const float *d_x, const float *d_dy, int64_t n, float *d_grad,
+                    float *d_scratch, size_t scratch_bytes, amr_stream stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step count t >= 1) on the mean over the
+   n samples of |y - d_y|^2; updates theta, the moments and the packed block; writes the
+   batch loss before the step to *d_loss (if not NULL). */
+amr_status mlp_train_step(float *d_theta, float *d_adam_m, float *d_adam_v, void *d_packed, const float *d_x,
+                          const float *d_y, int64_t n, float lr, int64_t t, float *d_loss, float *d_scratch,
+                          size_t scratch_bytes, amr_stream stream);
+
+/* Training data for the surrogate, harvested from the method's own runs: the FP64
+   Godunov kernel reconstructs every face of every level from d_u (with time step *d_dt)
+   and writes a deterministic one-in-`stride` sample of the floored face-normal states
+   (rho_L, u_L, p_L, rho_R, u_R, p_R) to d_states[capacity][6]; *d_count (caller zeroes
+   it) counts the sampled faces, possibly more than capacity (the rest are dropped).
+   d_u is not modified. */
+amr_status hydro_harvest_faces(const amr_tree *tree, const hydro_params *params, const double *d_u,
+                               const double *d_dt, double *d_states, int64_t capacity, int64_t stride,
+                               unsigned long long *d_count, amr_stream stream);
+
 /* Copy params->d_status and params->d_counters to the host (synchronises the device). */
 amr_status amr_get_status(const hydro_params *params, int32_t *h_status, unsigned long long *h_counters);
 

@@ -17,7 +17,10 @@ PREC_FP64, PREC_FP32 = 0, 1
 
 EXPORTS = ["amr_build_octree_query", "amr_build_octree", "hydro_init_from_prim", "hydro_prim_of_state",
            "hydro_courant", "hydro_godunov_level", "hydro_flux_reg_bytes", "hydro_reflux_level", "hydro_step",
-           "amr_get_status", "amr_status_string", "hydro_step_static_scratch"]
+           "amr_get_status", "amr_status_string", "hydro_step_static_scratch", "hydro_harvest_faces",
+           "mlp_nparams", "mlp_packed_bytes", "mlp_scratch_bytes", "mlp_pack", "mlp_make_dataset", "mlp_forward",
+           "mlp_grad", "mlp_train_step"]
+MLP_NPARAMS = 8962
 STATIC_REG_MAX_OCTS = 131072
 
 
@@ -68,11 +71,22 @@ def lib():
     L.hydro_reflux_level.argtypes = [PT, C.c_int, PP, P, P, P, P, P]
     L.hydro_step.argtypes = [PT, PP, P, P, P, P, P, P]
     L.hydro_step_static_scratch.argtypes = [PT, PP, P, P, P, P, P]
+    L.hydro_harvest_faces.argtypes = [PT, PP, P, P, P, C.c_int64, C.c_int64, P, P]
+    L.mlp_nparams.argtypes = []
+    L.mlp_packed_bytes.argtypes = []
+    L.mlp_packed_bytes.restype = S
+    L.mlp_scratch_bytes.argtypes = [C.c_int64]
+    L.mlp_scratch_bytes.restype = S
+    L.mlp_pack.argtypes = [P, P, P]
+    L.mlp_make_dataset.argtypes = [P, C.c_int64, C.c_double, P, P, P, P]
+    L.mlp_forward.argtypes = [P, P, P, C.c_int64, P]
+    L.mlp_grad.argtypes = [P, P, P, C.c_int64, P, P, S, P]
+    L.mlp_train_step.argtypes = [P, P, P, P, P, P, C.c_int64, C.c_float, C.c_int64, P, P, S, P]
     L.amr_get_status.argtypes = [PP, P, P]
     L.amr_status_string.argtypes = [C.c_int]
     L.amr_status_string.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("hydro_flux_reg_bytes", "amr_status_string"):
+        if name not in ("hydro_flux_reg_bytes", "amr_status_string", "mlp_packed_bytes", "mlp_scratch_bytes"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L

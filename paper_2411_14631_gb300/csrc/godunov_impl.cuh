@@ -13,6 +13,7 @@
 #pragma once
 #include <cfloat>
 #include "hydro_math.cuh"
+#include "mlp_warp.cuh"
 
 namespace amr {
 
@@ -44,6 +45,11 @@ struct GArgs {
     double gamma, rho_floor, p_floor, cfl;
     int32_t *status;
     unsigned long long *counters;
+    const void *mlp;          // packed surrogate weights (RS == AMR_RIEMANN_MLP)
+    float mlp_tol;            // residual acceptance threshold
+    double *harvest;          // if set: sampled face states [cap][6] are written, u_new is not
+    int64_t harvest_cap, harvest_stride;
+    unsigned long long *harvest_count;
 };
 
 // value of a neighbour of coarse leaf cell F (level lc, coordinates X) along axis d,
@@ -96,6 +102,9 @@ static __device__ void interp_child(const TreeView &tv, const double *__restrict
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
 
+// threads per CTA: depth-1 tiles (512 stencil cells) 128, depth-2 tiles (1728) 512
+template <int D> constexpr int threads_for() { return D == 1 ? 128 : 512; }
+
 template <typename R, int D, int RS>
 struct Smem {
     using G = Geo<D>;
@@ -103,14 +112,41 @@ struct Smem {
     R Q[4 * NV][G::NP];             // predicted state (5) + slopes (3 x 5)
     int32_t slot[G::NSLOT];
     uint8_t ref[G::NSLOT];
+    // surrogate staging, per warp: 32 faces x 8 features, then 32 x 2 outputs
+    float mlpx[RS == AMR_RIEMANN_MLP ? threads_for<D>() / 32 : 1][RS == AMR_RIEMANN_MLP ? 32 * 10 : 1];
     double dtmin[32];
 };
 
-// Riemann problem at face r0 of direction DIR: left state = predicted cell + half its
-// slope, right state = next cell - half its slope (floored), in the face-normal frame.
+// left and right states of face r0 of direction DIR (face-normal frame), floored
+template <typename R, int D, int RS, int DIR>
+__device__ __forceinline__ void face_states(const Smem<R, D, RS> &sm, int r0, const Prm<R> &pr, R WL[NV], R WR[NV])
+{
+    using G = Geo<D>;
+    const int fa = r0 % (G::CI + 1), t1 = (r0 / (G::CI + 1)) % G::CI, t2 = r0 / ((G::CI + 1) * G::CI);
+    const int Lx = DIR == 0 ? fa : 1 + t1;
+    const int Ly = DIR == 0 ? 1 + t1 : DIR == 1 ? fa : 1 + t2;
+    const int Lz = DIR == 2 ? fa : 1 + t2;
+    const int pl = Lx + G::P * (Ly + G::P * Lz);
+    const int pR = pl + (DIR == 0 ? 1 : DIR == 1 ? G::P : G::P * G::P);
+    constexpr int N0 = DIR + 1, T1 = DIR == 0 ? 2 : 1, T2 = DIR == 2 ? 2 : 3;
+    constexpr int S = NV + NV * DIR;
+    WL[0] = sm.Q[0][pl] + R(0.5) * sm.Q[S + 0][pl];
+    WR[0] = sm.Q[0][pR] - R(0.5) * sm.Q[S + 0][pR];
+    WL[1] = sm.Q[N0][pl] + R(0.5) * sm.Q[S + N0][pl];
+    WR[1] = sm.Q[N0][pR] - R(0.5) * sm.Q[S + N0][pR];
+    WL[2] = sm.Q[T1][pl] + R(0.5) * sm.Q[S + T1][pl];
+    WR[2] = sm.Q[T1][pR] - R(0.5) * sm.Q[S + T1][pR];
+    WL[3] = sm.Q[T2][pl] + R(0.5) * sm.Q[S + T2][pl];
+    WR[3] = sm.Q[T2][pR] - R(0.5) * sm.Q[S + T2][pR];
+    WL[4] = sm.Q[4][pl] + R(0.5) * sm.Q[S + 4][pl];
+    WR[4] = sm.Q[4][pR] - R(0.5) * sm.Q[S + 4][pR];
+    WL[0] = rmax(WL[0], pr.rho_floor); WR[0] = rmax(WR[0], pr.rho_floor);
+    WL[4] = rmax(WL[4], pr.p_floor); WR[4] = rmax(WR[4], pr.p_floor);
+}
+
 template <typename R, int D, int RS, int DIR>
 __device__ __forceinline__ void face_flux(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>::NF], int r0, const Prm<R> &pr,
-                                          int32_t *status)
+                                          int32_t *status, const GArgs &a, int64_t tile)
 {
     using G = Geo<D>;
     const int fa = r0 % (G::CI + 1), t1 = (r0 / (G::CI + 1)) % G::CI, t2 = r0 / ((G::CI + 1) * G::CI);
@@ -135,6 +171,20 @@ __device__ __forceinline__ void face_flux(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>
     WR[4] = sm.Q[4][pR] - R(0.5) * sm.Q[S + 4][pR];
     WL[0] = rmax(WL[0], pr.rho_floor); WR[0] = rmax(WR[0], pr.rho_floor);
     WL[4] = rmax(WL[4], pr.p_floor); WR[4] = rmax(WR[4], pr.p_floor);
+    if (a.harvest) {
+        // deterministic sample of the faces (hash of tile, direction and face)
+        uint64_t h = (uint64_t(tile) * 3 + DIR) * 0x9E3779B97F4A7C15ull + uint64_t(r0) * 0xBF58476D1CE4E5B9ull;
+        h ^= h >> 31;
+        if (h % uint64_t(a.harvest_stride) == 0) {
+            const unsigned long long k = atomicAdd(a.harvest_count, 1ull);
+            if (int64_t(k) < a.harvest_cap) {
+                double *o = a.harvest + 6 * int64_t(k);
+                o[0] = double(WL[0]); o[1] = double(WL[1]); o[2] = double(WL[4]);
+                o[3] = double(WR[0]); o[4] = double(WR[1]); o[5] = double(WR[4]);
+            }
+        }
+        return;
+    }
     R Fn[NV];
     if (RS == AMR_RIEMANN_EXACT) {
         R ps, us;
@@ -158,9 +208,93 @@ __device__ __forceinline__ void face_flux(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>
     sF[DIR][4][r0] = Fn[4];
 }
 
-// threads per CTA: depth-1 tiles (512 stencil cells) 128, depth-2 tiles (1728) 512
-template <int D> constexpr int threads_for() { return D == 1 ? 128 : 512; }
 
+// Riemann solve of the warp's 32 faces with the learned surrogate: features of each
+// face-normal problem, the network on the tensor cores (two groups of 16), then the
+// acceptance test -- p* > 0 and finite, |f(p*)| = |f_L + f_R + u_R - u_L| and
+// |u* - (u_L+u_R)/2 - (f_R - f_L)/2| both within tol * (c_L + c_R) (Toro Eq. 4.5, 4.9) --
+// sampling of the accepted (p*, u*) at x/t = 0, and the exact Newton solver for the rest.
+// All 32 lanes of the warp take part; lanes past the last face carry a dummy problem.
+template <typename R, int D, int RS>
+__device__ __forceinline__ void mlp_faces(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>::NF], const Prm<R> &pr,
+                                          const GArgs &a, unsigned &n_acc, unsigned &n_fb)
+{
+    using G = Geo<D>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float *stg = sm.mlpx[warp];
+    const mlp::Packed P = mlp::view(a.mlp);
+    for (int base = warp * 32; base < 3 * G::NF; base += nw * 32) {
+        const int f = base + lane;
+        const bool valid = f < 3 * G::NF;
+        const int d = valid ? f / G::NF : 0, r0 = valid ? f - d * G::NF : 0;
+        R WL[NV], WR[NV];
+        if (d == 0) face_states<R, D, RS, 0>(sm, r0, pr, WL, WR);
+        else if (d == 1) face_states<R, D, RS, 1>(sm, r0, pr, WL, WR);
+        else face_states<R, D, RS, 2>(sm, r0, pr, WL, WR);
+        R x[7], pref, ubar, cref;
+        mlp::features(WL[0], WL[1], WL[4], WR[0], WR[1], WR[4], pr.gamma, x, pref, ubar, cref);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) stg[lane * 8 + k] = float(x[k]);
+        stg[lane * 8 + 7] = 0.0f;
+        __syncwarp();
+        float o0[4], o1[4];
+        mlp::forward16(P, stg, lane, o0);
+        mlp::forward16(P, stg + 16 * 8, lane, o1);
+        if ((lane & 3) == 0) {
+            const int g = lane >> 2;
+            stg[256 + 2 * g] = o0[0]; stg[256 + 2 * g + 1] = o0[1];
+            stg[256 + 2 * (g + 8)] = o0[2]; stg[256 + 2 * (g + 8) + 1] = o0[3];
+            stg[256 + 2 * (g + 16)] = o1[0]; stg[256 + 2 * (g + 16) + 1] = o1[1];
+            stg[256 + 2 * (g + 24)] = o1[2]; stg[256 + 2 * (g + 24) + 1] = o1[3];
+        }
+        __syncwarp();
+        const R y0 = R(stg[256 + 2 * lane]), y1 = R(stg[256 + 2 * lane + 1]);
+        __syncwarp();
+        const R g = pr.gamma;
+        const R rL = WL[0], uL = WL[1], pL = WL[4], rR = WR[0], uR = WR[1], pR = WR[4];
+        const R cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+        const bool vac = R(2) * (cL + cR) / (g - R(1)) <= uR - uL;
+        const R ps = pref * exp(y0), us = ubar + cref * y1;
+        bool ok = !vac && isfinite(ps) && ps > R(0) && isfinite(us);
+        if (ok) {
+            R fL, dfL, fR, dfR;
+            side_f(ps, rL, pL, cL, g, fL, dfL);
+            side_f(ps, rR, pR, cR, g, fR, dfR);
+            const R tolc = R(a.mlp_tol) * (cL + cR);
+            ok = fabs(fL + fR + (uR - uL)) <= tolc && fabs(us - (R(0.5) * (uL + uR) + R(0.5) * (fR - fL))) <= tolc;
+        }
+        R Fn[NV], W0[NV], U0[NV];
+        if (ok) {
+            exact_sample0(WL, WR, g, ps, us, W0);
+            flux_normal(W0, g, Fn, U0);
+        } else {
+            R ps2, us2;
+            const R tol = sizeof(R) == 8 ? R(1e-14) : R(1e-6);
+            const int e = exact_star(WL, WR, g, tol, 50, ps2, us2);
+            if (e == 0) {
+                exact_sample0(WL, WR, g, ps2, us2, W0);
+                flux_normal(W0, g, Fn, U0);
+            } else {
+                if (valid) set_error(a.status, e);
+                hllc(WL, WR, g, Fn);
+            }
+        }
+        const unsigned acc = __ballot_sync(0xffffffffu, ok && valid), fb = __ballot_sync(0xffffffffu, !ok && valid);
+        n_acc += __popc(acc);
+        n_fb += __popc(fb);
+        if (valid) {
+            const int N0 = d + 1, T1 = d == 0 ? 2 : 1, T2 = d == 2 ? 2 : 3;
+            sF[d][0][r0] = Fn[0];
+            sF[d][N0][r0] = Fn[1];
+            sF[d][T1][r0] = Fn[2];
+            sF[d][T2][r0] = Fn[3];
+            sF[d][4][r0] = Fn[4];
+        }
+    }
+}
+
+// Riemann problem at face r0 of direction DIR: left state = predicted cell + half its
+// slope, right state = next cell - half its slope (floored), in the face-normal frame.
 template <typename R, int D, int RS>
 __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
 {
@@ -176,6 +310,7 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
     pr.gamma = to_work<R>(a.gamma); pr.rho_floor = to_work<R>(a.rho_floor); pr.p_floor = to_work<R>(a.p_floor);
     const R cflR = to_work<R>(a.cfl);
 
+    unsigned n_acc = 0, n_fb = 0;   // surrogate: accepted faces, fallbacks (counted by lane 0)
     for (int64_t t = a.t_begin + blockIdx.x; t < a.t_end; t += gridDim.x) {
         // ---- level of this tile and its geometry
         int l = a.lfirst;
@@ -271,13 +406,18 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
         __syncthreads();
 
         // ---- phase 3: Riemann problem at every face touching an updated cell
-        for (int f = tid; f < 3 * G::NF; f += blockDim.x) {
-            const int d = f / G::NF, r0 = f - d * G::NF;
-            if (d == 0) face_flux<R, D, RS, 0>(sm, sF, r0, pr, a.status);
-            else if (d == 1) face_flux<R, D, RS, 1>(sm, sF, r0, pr, a.status);
-            else face_flux<R, D, RS, 2>(sm, sF, r0, pr, a.status);
+        if constexpr (RS == AMR_RIEMANN_MLP) {
+            mlp_faces<R, D, RS>(sm, sF, pr, a, n_acc, n_fb);
+        } else {
+            for (int f = tid; f < 3 * G::NF; f += blockDim.x) {
+                const int d = f / G::NF, r0 = f - d * G::NF;
+                if (d == 0) face_flux<R, D, RS, 0>(sm, sF, r0, pr, a.status, a, t);
+                else if (d == 1) face_flux<R, D, RS, 1>(sm, sF, r0, pr, a.status, a, t);
+                else face_flux<R, D, RS, 2>(sm, sF, r0, pr, a.status, a, t);
+            }
         }
         __syncthreads();
+        if (a.harvest) continue;   // harvesting only: no update (the loop ends with no barrier due)
 
         // ---- phase 4: FP64 update of existing cells + fused CFL candidate
         // new states of octs whose father is restricted here, in the (now free) predictor buffer
@@ -383,6 +523,10 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
         }
         __syncthreads();
     }
+    if (RS == AMR_RIEMANN_MLP && a.counters && (tid & 31) == 0 && (n_acc | n_fb)) {
+        atomicAdd(a.counters + 0, (unsigned long long)n_acc);
+        atomicAdd(a.counters + 1, (unsigned long long)n_fb);
+    }
 }
 
 template <typename R, int D, int RS>
@@ -428,13 +572,55 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
         a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
         a.status = p->d_status; a.counters = p->d_counters;
         const int64_t nt = a.t_end - a.t_begin;
-        const bool ex = p->riemann == AMR_RIEMANN_EXACT;
+        a.mlp = p->mlp_weights;
+        a.mlp_tol = p->mlp_resid_tol;
+        a.harvest = nullptr;
+        a.harvest_cap = 0;
+        a.harvest_stride = 1;
+        a.harvest_count = nullptr;
+        constexpr int D2 = 2 - (sizeof(R) == 8);
         amr_status r;
-        if (d == 1) r = ex ? launch<R, 1, 1>(a, nt, st) : launch<R, 1, 0>(a, nt, st);
-        else r = ex ? launch<R, 2 - (sizeof(R) == 8), 1>(a, nt, st) : launch<R, 2 - (sizeof(R) == 8), 0>(a, nt, st);
+        if (p->riemann == AMR_RIEMANN_MLP) {
+            if (sizeof(R) == 8 || !p->mlp_weights) return AMR_EINVAL;   // the surrogate runs in the FP32 path
+            // the network's fragments need the register budget of 128-thread CTAs: depth-1 tiles
+            if (d != 1) {
+                a.tile_root = t->tile_root[0];
+                a.tile_slot = t->tile_slot[0];
+                for (int i = 0; i < AMR_MAXLEV + 2; ++i) a.tile_off[i] = t->tile_off[0][i];
+                a.t_begin = t->tile_off[0][la];
+                a.t_end = t->tile_off[0][lb + 1];
+            }
+            r = launch<R, 1, AMR_RIEMANN_MLP>(a, a.t_end - a.t_begin, st);
+        } else if (p->riemann == AMR_RIEMANN_EXACT) {
+            r = d == 1 ? launch<R, 1, AMR_RIEMANN_EXACT>(a, nt, st) : launch<R, D2, AMR_RIEMANN_EXACT>(a, nt, st);
+        } else {
+            r = d == 1 ? launch<R, 1, AMR_RIEMANN_HLLC>(a, nt, st) : launch<R, D2, AMR_RIEMANN_HLLC>(a, nt, st);
+        }
         if (r != AMR_OK) return r;
     }
     return AMR_OK;
+}
+
+// Face-state harvest: the FP64 depth-1 kernel through phase 2, writing a deterministic
+// sample (one face in `stride`) of the floored face-normal states, no update.
+inline amr_status harvest_impl(const amr_tree *t, const hydro_params *p, const double *u, const double *dt,
+                               double *out, int64_t cap, int64_t stride, unsigned long long *count, cudaStream_t st)
+{
+    GArgs a;
+    a.tv = make_view(t);
+    a.tile_root = t->tile_root[0];
+    a.tile_slot = t->tile_slot[0];
+    for (int i = 0; i < AMR_MAXLEV + 2; ++i) a.tile_off[i] = t->tile_off[0][i];
+    a.lfirst = t->levelmin;
+    a.llast = t->levelmax;
+    a.t_begin = t->tile_off[0][t->levelmin];
+    a.t_end = t->tile_off[0][t->levelmax + 1];
+    a.u_old = u; a.u_new = nullptr; a.reg = nullptr; a.dt = dt; a.dt_next = nullptr;
+    a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
+    a.status = p->d_status; a.counters = nullptr;
+    a.mlp = nullptr; a.mlp_tol = 0.0f;
+    a.harvest = out; a.harvest_cap = cap; a.harvest_stride = stride; a.harvest_count = count;
+    return launch<double, 1, AMR_RIEMANN_HLLC>(a, a.t_end - a.t_begin, st);
 }
 
 }  // namespace amr

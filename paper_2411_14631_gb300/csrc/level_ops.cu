@@ -7,6 +7,8 @@
 namespace amr {
 amr_status godunov_dispatch_fp32(const amr_tree *t, int level, const hydro_params *p, const double *u_old,
                                  double *u_new, double *reg, const double *dt, double *dt_next, cudaStream_t st);
+amr_status harvest_dispatch(const amr_tree *t, const hydro_params *p, const double *u, const double *dt, double *out,
+                            int64_t cap, int64_t stride, unsigned long long *count, cudaStream_t st);
 amr_status godunov_dispatch_fp64(const amr_tree *t, int level, const hydro_params *p, const double *u_old,
                                  double *u_new, double *reg, const double *dt, double *dt_next, cudaStream_t st);
 
@@ -216,7 +218,7 @@ extern "C" amr_status hydro_godunov_level(const amr_tree *t, int level, const hy
                                           amr_stream stream)
 {
     if (check(t, p) != AMR_OK || !d_u_old || !d_u_new || !d_dt) return AMR_EINVAL;
-    if (p->riemann == AMR_RIEMANN_MLP) return AMR_EINVAL;   // the surrogate runs through its own entry points
+    if (p->riemann == AMR_RIEMANN_MLP && (p->precision != AMR_PREC_FP32 || !p->mlp_weights)) return AMR_EINVAL;
     if (level != -1 && (level < t->levelmin || level > t->levelmax)) return AMR_EINVAL;
     if (t->levelmax > t->levelmin && !d_flux_reg) return AMR_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -270,6 +272,16 @@ extern "C" amr_status hydro_step_static_scratch(const amr_tree *t, const hydro_p
         g_static_reg_addr[dev] = static_cast<double *>(addr);
     }
     return hydro_step(t, p, d_u_old, d_u_new, g_static_reg_addr[dev], d_dt, d_dt_next, stream);
+}
+
+extern "C" amr_status hydro_harvest_faces(const amr_tree *t, const hydro_params *p, const double *d_u,
+                                          const double *d_dt, double *d_states, int64_t capacity, int64_t stride,
+                                          unsigned long long *d_count, amr_stream stream)
+{
+    if (check(t, p) != AMR_OK || !d_u || !d_dt || !d_states || !d_count || capacity < 0 || stride < 1)
+        return AMR_EINVAL;
+    return harvest_dispatch(t, p, d_u, d_dt, d_states, capacity, stride, d_count,
+                            reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" amr_status amr_get_status(const hydro_params *p, int32_t *h_status, unsigned long long *h_counters)

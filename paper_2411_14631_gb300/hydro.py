@@ -126,6 +126,91 @@ def hydro_step_static_scratch(tree, prm, u_old, u_new, dt, dt_next=None, stream=
                                           _ptr(dt_next), _stream(stream)))
 
 
+def hydro_harvest_faces(tree, prm, u, dt, states, stride, count, stream=None):
+    """Sampled face-normal (L, R) states of one reconstruction of u (see include/amrhydro.h)."""
+    check("hydro_harvest_faces",
+          lib().hydro_harvest_faces(C.byref(tree.t), C.byref(prm.c), _ptr(u), _ptr(dt), _ptr(states),
+                                    states.shape[0], stride, _ptr(count), _stream(stream)))
+
+
+def mlp_pack(theta, packed, stream=None):
+    check("mlp_pack", lib().mlp_pack(_ptr(theta), _ptr(packed), _stream(stream)))
+
+
+def mlp_make_dataset(states, gamma, x, y, status=None, stream=None):
+    check("mlp_make_dataset", lib().mlp_make_dataset(_ptr(states), states.shape[0], gamma, _ptr(x), _ptr(y),
+                                                     _ptr(status), _stream(stream)))
+
+
+def mlp_forward(packed, x, y, stream=None):
+    check("mlp_forward", lib().mlp_forward(_ptr(packed), _ptr(x), _ptr(y), x.shape[0], _stream(stream)))
+
+
+def mlp_grad(packed, x, dy, grad, scratch, stream=None):
+    check("mlp_grad", lib().mlp_grad(_ptr(packed), _ptr(x), _ptr(dy), x.shape[0], _ptr(grad), _ptr(scratch),
+                                     scratch.numel() * 4, _stream(stream)))
+
+
+def mlp_train_step(theta, m, v, packed, x, y, lr, t, loss, scratch, stream=None):
+    check("mlp_train_step", lib().mlp_train_step(_ptr(theta), _ptr(m), _ptr(v), _ptr(packed), _ptr(x), _ptr(y),
+                                                 x.shape[0], lr, t, _ptr(loss), _ptr(scratch), scratch.numel() * 4,
+                                                 _stream(stream)))
+
+
+class Surrogate:
+    """The learned Riemann surrogate's device state: FP32 master parameters, Adam
+    moments and the packed BF16 block the kernels read.  Initial weights: seeded
+    Gaussian, std 1/sqrt(fan_in), zero biases."""
+
+    def __init__(self, seed=4, device="cuda:0", theta=None):
+        n = int(lib().mlp_nparams())
+        self.device = torch.device(device)
+        if theta is None:
+            rng = np.random.default_rng(seed)
+            th = np.zeros(n, dtype=np.float32)
+            shapes = [(64, 7), (64,), (64, 64), (64,), (64, 64), (64,), (2, 64), (2,)]
+            o = 0
+            for sh in shapes:
+                size = int(np.prod(sh))
+                if len(sh) == 2:
+                    th[o:o + size] = rng.normal(0.0, 1.0 / np.sqrt(sh[1]), size)
+                o += size
+            theta = th
+        self.theta = torch.as_tensor(np.asarray(theta, dtype=np.float32)).to(self.device)
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.packed = torch.empty(int(lib().mlp_packed_bytes()), dtype=torch.uint8, device=self.device)
+        self.t = 0
+        mlp_pack(self.theta, self.packed)
+
+    def forward(self, x):
+        y = torch.empty((x.shape[0], 2), dtype=torch.float32, device=self.device)
+        mlp_forward(self.packed, x, y)
+        return y
+
+    def train(self, x, y, epochs=1, batch=4096, lr=1e-3, seed=0, lr_final=None):
+        """Adam over shuffled minibatches; returns the mean loss of each epoch."""
+        n = x.shape[0]
+        scratch = torch.empty(int(lib().mlp_scratch_bytes(batch)) // 4 + 1, dtype=torch.float32, device=self.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        gen = torch.Generator(device="cpu").manual_seed(seed)
+        hist = []
+        nb = max(1, n // batch)
+        total = epochs * nb
+        for ep in range(epochs):
+            perm = torch.randperm(n, generator=gen).to(self.device)
+            xs, ys = x[perm].contiguous(), y[perm].contiguous()
+            acc = torch.zeros(1, dtype=torch.float32, device=self.device)
+            for b in range(nb):
+                self.t += 1
+                rate = lr if lr_final is None else lr * (lr_final / lr) ** (min(self.t, total) / total)
+                mlp_train_step(self.theta, self.m, self.v, self.packed, xs[b * batch:(b + 1) * batch],
+                               ys[b * batch:(b + 1) * batch], rate, self.t, loss, scratch)
+                acc += loss
+            hist.append(float(acc.item()) / nb)
+        return hist
+
+
 class Simulation:
     """State buffers and the step sequence of one run (u_old -> u_new, dt on the device).
 

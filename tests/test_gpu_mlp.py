@@ -1,0 +1,186 @@
+"""The learned Riemann surrogate on the GPU against the FP64 oracle.
+
+BF16 weights and activations with FP32 accumulation: forward outputs within 3e-2 of the
+oracle's FP64 network (relative to the output scale), parameter gradients within 3e-2 in
+norm.  Dataset labels (exact FP64 solver on the GPU) match the oracle's exact solver to
+1e-12.  Adam in FP32 matches the oracle's FP64 Adam to 1e-6.  Inside the Godunov update:
+with a zero acceptance threshold every face falls back to the exact solver, so the
+result equals the exact-solver path bit for bit; with a trained network most faces are
+accepted and the result stays close to the exact-solver path."""
+import numpy as np
+import pytest
+
+from paper_2411_14631_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_14631_gb300 import build
+    build.build()
+    from paper_2411_14631_gb300 import hydro
+    return hydro
+
+
+def _random_states(n, seed):
+    rng = np.random.default_rng(seed)
+    rL = np.exp(rng.normal(0, 1, n)); rR = np.exp(rng.normal(0, 1, n))
+    pL = np.exp(rng.normal(0, 1, n)); pR = np.exp(rng.normal(0, 1, n))
+    uL = rng.normal(0, 1, n); uR = rng.normal(0, 1, n)
+    return np.stack([rL, uL, pL, rR, uR, pR], axis=1)
+
+
+def _x8(x7):
+    x = np.zeros((x7.shape[0], 8), np.float32)
+    x[:, :7] = x7
+    return x
+
+
+def test_forward_matches_oracle(oracle, H):
+    import torch
+    sur = H.Surrogate(seed=1)
+    th = sur.theta.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(3)
+    x7 = rng.normal(0, 1, (1000, 7)); x7[:, 6] = rng.uniform(1.1, 1.7, 1000)
+    y_o = oracle.mlp_forward(th, x7)
+    y_g = sur.forward(torch.as_tensor(_x8(x7)).cuda()).cpu().numpy()
+    scale = np.abs(y_o).max()
+    assert np.abs(y_g - y_o).max() <= 3e-2 * scale, np.abs(y_g - y_o).max() / scale
+    # odd batch sizes and a ragged tail
+    y_g2 = sur.forward(torch.as_tensor(_x8(x7[:37])).cuda()).cpu().numpy()
+    assert np.array_equal(y_g2, y_g[:37])
+
+
+def test_gradient_matches_oracle(oracle, H):
+    import torch
+    from paper_2411_14631_gb300.abi import lib
+    sur = H.Surrogate(seed=2)
+    th = sur.theta.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(4)
+    n = 300                                     # several 128-sample chunks and a ragged tail
+    x7 = rng.normal(0, 1, (n, 7)); x7[:, 6] = 1.4
+    dy = rng.normal(0, 1, (n, 2))
+    g_o = oracle.mlp_backward(th, x7, dy)
+    grad = torch.empty(th.size, dtype=torch.float32, device="cuda")
+    scratch = torch.empty(int(lib().mlp_scratch_bytes(n)) // 4 + 1, dtype=torch.float32, device="cuda")
+    H.mlp_grad(sur.packed, torch.as_tensor(_x8(x7)).cuda(), torch.as_tensor(dy.astype(np.float32)).cuda(), grad,
+               scratch)
+    g_g = grad.cpu().numpy()
+    rel = np.linalg.norm(g_g - g_o) / np.linalg.norm(g_o)
+    assert rel <= 3e-2, rel
+    # every block of parameters is reached (weights and biases of all four layers)
+    offs = [0, 448, 512, 4608, 4672, 8768, 8832, 8960, 8962]
+    for a, b in zip(offs[:-1], offs[1:]):
+        blk = np.linalg.norm(g_g[a:b] - g_o[a:b]) / (np.linalg.norm(g_o[a:b]) + 1e-30)
+        assert blk <= 5e-2, (a, b, blk)
+
+
+def test_dataset_labels_match_oracle_exact_solver(oracle, H):
+    import torch
+    st = _random_states(2000, 5)
+    x = torch.empty((2000, 8), dtype=torch.float32, device="cuda")
+    y = torch.empty((2000, 2), dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    keep = []
+    for i in range(2000):
+        WL = np.array([st[i, 0], st[i, 1], 0, 0, st[i, 2]]); WR = np.array([st[i, 3], st[i, 4], 0, 0, st[i, 5]])
+        keep.append(oracle.exact_star(WL, WR, 1.4)[2] == 0)
+    keep = np.array(keep)
+    stk = np.ascontiguousarray(st[keep])
+    H.mlp_make_dataset(torch.as_tensor(stk).cuda(), 1.4, x[:keep.sum()], y[:keep.sum()], status)
+    assert status.item() == 0
+    xg, yg = x[:keep.sum()].cpu().numpy(), y[:keep.sum()].cpu().numpy()
+    for i in range(0, stk.shape[0], 37):
+        WL = np.array([stk[i, 0], stk[i, 1], 0, 0, stk[i, 2]]); WR = np.array([stk[i, 3], stk[i, 4], 0, 0, stk[i, 5]])
+        xo, ref = oracle.mlp_features(WL, WR, 1.4)
+        ps, us, _, _ = oracle.exact_star(WL, WR, 1.4)
+        assert np.allclose(xg[i, :7], xo, rtol=1e-6, atol=1e-6)
+        assert abs(yg[i, 0] - np.log(ps / ref[0])) <= 1e-6 * (1 + abs(np.log(ps / ref[0])))
+        assert abs(yg[i, 1] - (us - ref[1]) / ref[2]) <= 1e-6 * (1 + abs((us - ref[1]) / ref[2]))
+
+
+def test_adam_step_matches_oracle(oracle, H):
+    import torch
+    from paper_2411_14631_gb300.abi import lib
+    sur = H.Surrogate(seed=6)
+    th0 = sur.theta.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(7)
+    n = 256
+    x = torch.as_tensor(_x8(np.concatenate([rng.normal(0, 1, (n, 6)), np.full((n, 1), 1.4)], axis=1))).cuda()
+    t = torch.as_tensor(rng.normal(0, 1, (n, 2)).astype(np.float32)).cuda()
+    # the gradient the step will use: d/dtheta of mean |y - t|^2 = sum dy . y with dy = 2 (y - t) / n
+    y = sur.forward(x)
+    dy = 2.0 * (y - t) / n
+    grad = torch.empty(sur.theta.numel(), dtype=torch.float32, device="cuda")
+    scratch = torch.empty(int(lib().mlp_scratch_bytes(n)) // 4 + 1, dtype=torch.float32, device="cuda")
+    H.mlp_grad(sur.packed, x, dy, grad, scratch)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    H.mlp_train_step(sur.theta, sur.m, sur.v, sur.packed, x, t, 1e-3, 1, loss, scratch)
+    th_o, m_o, v_o = th0.copy(), np.zeros_like(th0), np.zeros_like(th0)
+    oracle.adam_step(th_o, m_o, v_o, grad.cpu().numpy().astype(np.float64), 1e-3, 0.9, 0.999, 1e-8, 1)
+    assert np.abs(sur.theta.cpu().numpy() - th_o).max() <= 1e-6
+    assert abs(loss.item() - float(((y - t) ** 2).sum().item()) / n) <= 1e-4 * loss.item()
+
+
+def _harvest_sod(H, n_keep=60000):
+    import torch
+    from paper_2411_14631_gb300.bench_util import cell_centres_of
+    tree = H.Octree(W.uniform_tree(5), 5, (1,) * 6)
+    prm = H.Params(1.4, cfl=0.8)
+    sim = H.Simulation(tree, prm, w0=W.sod_prims(cell_centres_of(tree)))
+    states = torch.empty((n_keep, 6), dtype=torch.float64, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    per_step = n_keep // 20
+    chunks = []
+    for _ in range(20):
+        count.zero_()
+        H.hydro_harvest_faces(tree, prm, sim.u, sim.dt, states[:per_step], 4, count)
+        k = min(int(count.item()), per_step)
+        chunks.append(states[:k].clone())
+        sim.step()
+    return torch.cat(chunks)
+
+
+def test_godunov_with_surrogate(oracle, H):
+    import torch
+    from paper_2411_14631_gb300.bench_util import cell_centres_of
+    from paper_2411_14631_gb300 import abi
+    st = _harvest_sod(H)
+    assert st.shape[0] > 10000
+    x = torch.empty((st.shape[0], 8), dtype=torch.float32, device="cuda")
+    y = torch.empty((st.shape[0], 2), dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    H.mlp_make_dataset(st, 1.4, x, y, status)
+    assert status.item() == 0
+    sur = H.Surrogate(seed=4)
+    hist = sur.train(x, y, epochs=12, batch=2048, lr=3e-3, lr_final=3e-4)
+    assert hist[-1] < 0.05 * hist[0], hist
+
+    tree = H.Octree(W.uniform_tree(5), 5, (1,) * 6)
+    w0 = W.sod_prims(cell_centres_of(tree))
+    res = {}
+    for name, riemann, tol in (("exact", abi.RIEMANN_EXACT, 0.0), ("mlp_tol0", abi.RIEMANN_MLP, 0.0),
+                               ("mlp", abi.RIEMANN_MLP, 0.05), ("hllc", abi.RIEMANN_HLLC, 0.0)):
+        prm = H.Params(1.4, cfl=0.8, riemann=riemann, precision=abi.PREC_FP32)
+        prm.c.mlp_weights = sur.packed.data_ptr()
+        prm.c.mlp_resid_tol = tol
+        sim = H.Simulation(tree, prm, w0=w0)
+        for _ in range(10):
+            sim.step()
+        torch.cuda.synchronize()
+        res[name] = (sim.u.cpu().numpy(), prm.read_status())
+    # zero threshold: every face solved exactly -> identical to the exact-solver path
+    assert np.array_equal(res["mlp_tol0"][0], res["exact"][0])
+    st0, cnt0 = res["mlp_tol0"][1]
+    assert st0 == 0 and cnt0[0] == 0 and cnt0[1] > 0
+    # trained network: most faces accepted, result close to the exact-solver path
+    st1, cnt1 = res["mlp"][1]
+    assert st1 == 0 and cnt1[0] > 0.5 * (cnt1[0] + cnt1[1]), cnt1
+    ue, um, uh = res["exact"][0], res["mlp"][0], res["hllc"][0]
+    l1_mlp = np.abs(um[0] - ue[0]).sum() / np.abs(ue[0]).sum()
+    l1_hllc = np.abs(uh[0] - ue[0]).sum() / np.abs(ue[0]).sum()
+    assert l1_mlp < 1e-3, (l1_mlp, l1_hllc)

@@ -158,6 +158,22 @@ def time_path(H, tree, prm, w0, steps, warmup, stream, label, kernel_events=True
     return ms, gms, sim, launches_per_step
 
 
+def time_graph(H, tree, prm, w0, steps, warmup):
+    """Whole steps replayed from CUDA graphs (two graphs, alternating state buffers)."""
+    import torch
+    sim = H.Simulation(tree, prm, w0=w0).use_graph()
+    for _ in range(warmup):
+        sim.step()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    for _ in range(steps):
+        sim.step()
+    t1.record()
+    t1.synchronize()
+    return t0.elapsed_time(t1) / steps, sim
+
+
 def time_e2e(H, tree, prm, w0, steps, stream):
     """Public-API end to end: per step, H2D of the state from pinned host memory,
     hydro_step, D2H of the new state to pinned host memory."""
@@ -246,6 +262,138 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def l1_fields(u, ref):
+    """Relative L1 of rho, |momentum| and E over the (equal-volume) leaf cells."""
+    import torch
+    mom = torch.sqrt(u[1] ** 2 + u[2] ** 2 + u[3] ** 2)
+    momr = torch.sqrt(ref[1] ** 2 + ref[2] ** 2 + ref[3] ** 2)
+    out = {}
+    for name, a, b in (("rho", u[0], ref[0]), ("mom", mom, momr), ("E", u[4], ref[4])):
+        out[name] = float((torch.abs(a - b).sum() / torch.abs(b).sum()).item())
+    return out
+
+
+def study_surrogate(args):
+    """Learned Riemann surrogate study on the turbulent 256^3 box: harvest, label, train,
+    then exact vs surrogate+fallback vs HLLC against the FP64 exact-solver reference."""
+    import numpy as np
+    import torch
+    from paper_2411_14631_gb300 import build, abi
+    build.build()
+    from paper_2411_14631_gb300 import hydro as H
+    from paper_2411_14631_gb300 import workloads as W
+    from paper_2411_14631_gb300.bench_util import cell_centres_of
+    torch.cuda.set_device(0)
+    out = {"study": "learned Riemann surrogate (BF16 tensor-core MLP + exact fallback)", "data": "synthetic"}
+    lx, rho, v = make_workload()
+    tree = H.Octree(lx, LEVEL, (abi.BC_PERIODIC,) * 6)
+    w0 = prims_for(cell_centres_of(tree), rho, v)
+    # ---- harvest from FP64 runs: the turbulent box (10 steps) and the Sod tube (20 steps)
+    t0 = time.perf_counter()
+    per_step = args.harvest // 10
+    chunks = []
+    prm64 = H.Params(GAMMA, cfl=CFL)
+    sim = H.Simulation(tree, prm64, w0=w0)
+    buf = torch.empty((per_step, 6), dtype=torch.float64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stride = max(1, int(3.75 * leaf_count(tree) / per_step))
+    for _ in range(10):
+        cnt.zero_()
+        H.hydro_harvest_faces(tree, prm64, sim.u, sim.dt, buf, stride, cnt)
+        chunks.append(buf[:min(per_step, int(cnt.item()))].clone())
+        sim.step()
+    del sim
+    sod_tree = H.Octree(W.uniform_tree(5), 5, (abi.BC_OUTFLOW,) * 6)
+    prm_sod = H.Params(1.4, cfl=CFL)
+    sim = H.Simulation(sod_tree, prm_sod, w0=W.sod_prims(cell_centres_of(sod_tree)))
+    sod = []
+    for _ in range(20):
+        cnt.zero_()
+        H.hydro_harvest_faces(sod_tree, prm_sod, sim.u, sim.dt, buf, 1, cnt)
+        sod.append(buf[:min(per_step, int(cnt.item()))].clone())
+        sim.step()
+    turb = torch.unique(torch.cat(chunks), dim=0)
+    sod = torch.unique(torch.cat(sod), dim=0)
+    g = torch.Generator(device="cpu").manual_seed(4)
+    sod = sod[torch.randperm(sod.shape[0], generator=g)[:max(1, turb.shape[0] // 99)].cuda()]
+    states = torch.cat([turb, sod])
+    perm = torch.randperm(states.shape[0], generator=g).cuda()
+    states = states[perm].contiguous()
+    # both workloads' gammas appear in the set: the turbulent faces at 5/3, the Sod faces at 1.4
+    n = states.shape[0]
+    n_turb = turb.shape[0]
+    gam = torch.where(perm < n_turb, torch.tensor(GAMMA, device="cuda"), torch.tensor(1.4, device="cuda"))
+    x = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    y = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for gval in (GAMMA, 1.4):
+        idx = torch.nonzero(gam == gval).flatten()
+        xs = torch.empty((idx.numel(), 8), dtype=torch.float32, device="cuda")
+        ys = torch.empty((idx.numel(), 2), dtype=torch.float32, device="cuda")
+        H.mlp_make_dataset(states[idx].contiguous(), gval, xs, ys, status)
+        x[idx] = xs
+        y[idx] = ys
+    out["harvest"] = {"faces": n, "turbulent": n_turb, "sod": int(sod.shape[0]), "stride": stride,
+                      "status": int(status.item()), "seconds": time.perf_counter() - t0}
+    ntr = int(0.9 * n)
+    sur = H.Surrogate(seed=4)
+    t1 = time.perf_counter()
+    hist = sur.train(x[:ntr], y[:ntr], epochs=args.epochs, batch=4096, lr=3e-3, lr_final=1e-4, seed=4)
+    torch.cuda.synchronize()
+    ttrain = time.perf_counter() - t1
+    yv = sur.forward(x[ntr:])
+    val = float(((yv - y[ntr:]) ** 2).sum(dim=1).mean().item())
+    out["training"] = {"samples": ntr, "epochs": args.epochs, "batch": 4096, "loss_first_epoch": hist[0],
+                       "loss_last_epoch": hist[-1], "val_loss": val, "seconds": ttrain,
+                       "samples_per_s": ntr * args.epochs / ttrain}
+    # ---- 10 steps at a common fixed dt: the reference and the paths reach the same time
+    dt0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    H.hydro_courant(tree, H.Params(GAMMA, cfl=CFL, precision=abi.PREC_FP32), H.Simulation(tree, prm64, w0=w0).u, dt0)
+    dt_fixed = float(dt0.item()) * 0.75
+    dt = torch.full((1,), dt_fixed, dtype=torch.float64, device="cuda")
+
+    def run(prm, steps=10):
+        s_ = H.Simulation(tree, prm, w0=w0)
+        for _ in range(steps):
+            H.hydro_step(tree, prm, s_.u, s_.u_new, s_.reg, dt, None)
+            s_.u, s_.u_new = s_.u_new, s_.u
+        torch.cuda.synchronize()
+        return s_.u
+
+    ref = run(H.Params(GAMMA, cfl=CFL, riemann=abi.RIEMANN_EXACT))
+    paths = {}
+    for name, riemann, prec in (("exact_fp32", abi.RIEMANN_EXACT, abi.PREC_FP32),
+                                ("mlp_fallback_fp32", abi.RIEMANN_MLP, abi.PREC_FP32),
+                                ("hllc_fp32", abi.RIEMANN_HLLC, abi.PREC_FP32),
+                                ("hllc_fp64_plain", abi.RIEMANN_HLLC, abi.PREC_FP64)):
+        prm = H.Params(GAMMA, cfl=CFL, riemann=riemann, precision=prec)
+        prm.c.mlp_weights = sur.packed.data_ptr()
+        prm.c.mlp_resid_tol = args.tol
+        u = run(prm)
+        st, cntr = prm.read_status()
+        prm.clear_status()
+        ms, _ = time_graph(H, tree, prm, w0, 5, 2)
+        st2, cntr2 = prm.read_status()
+        rec = {"l1_vs_fp64_exact": l1_fields(u, ref), "ms_per_step": ms,
+               "cell_updates_per_s": leaf_count(tree) / (ms * 1e-3), "status": st}
+        if riemann == abi.RIEMANN_MLP:
+            tot = cntr[0] + cntr[1]
+            rec["faces_accepted"] = cntr[0]
+            rec["fallbacks"] = cntr[1]
+            rec["fallback_rate"] = cntr[1] / max(1, tot)
+            rec["tol"] = args.tol
+        paths[name] = rec
+    out["paths"] = paths
+    out["reference"] = "FP64 exact-solver path on the GPU (equal to the oracle within 1e-12), 10 steps, fixed dt"
+    out["dt_fixed"] = dt_fixed
+    print(json.dumps(out))
+    return 0
+
+
+def leaf_count(tree):
+    return tree.leaf_cells()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -256,8 +404,14 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--study", default=None, choices=["surrogate"])
+    ap.add_argument("--harvest", type=int, default=10_000_000)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--tol", type=float, default=0.02)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
+    if args.study == "surrogate":
+        return study_surrogate(args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
 
@@ -279,7 +433,12 @@ def main():
     w0 = prims_for(xyz, rho, v)
     leaf = tree.leaf_cells()
 
-    prm32 = H.Params(GAMMA, cfl=CFL, precision=abi.PREC_FP32, tile=args.tile, device=dev)
+    tile = args.tile
+    tune_ms = None
+    if tile == 0:
+        from paper_2411_14631_gb300 import autotune
+        tile, tune_ms = autotune.tune(tree, GAMMA, w0, precision=abi.PREC_FP32, cfl=CFL)
+    prm32 = H.Params(GAMMA, cfl=CFL, precision=abi.PREC_FP32, tile=tile, device=dev)
     clk = Clocks(local)
 
     def barrier():
@@ -287,9 +446,11 @@ def main():
         if ws > 1:
             torch.distributed.barrier()
 
+    # per-kernel timing (eager launches, events around the update kernel)
+    _, gms, _, lps = time_path(H, tree, prm32, w0, args.steps, args.warmup, stream, "fp32")
     barrier()
     clk.start()
-    ms, gms, sim32, lps = time_path(H, tree, prm32, w0, args.steps, args.warmup, stream, "fp32")
+    ms, sim32 = time_graph(H, tree, prm32, w0, args.steps, args.warmup)
     barrier()
     clocks = clk.stop()
     if ws > 1:
@@ -312,7 +473,8 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "leaf_cells": leaf, "octs": tree.noct,
                       "precision": "FP32 reconstruction + Riemann, FP64 state accumulation",
-                      "tile_depth": args.tile or 1, "parallelism": "replicas" if ws > 1 else "single GPU",
+                      "tile_depth": tile, "autotune_ms_per_step": tune_ms, "cuda_graph": True,
+                      "parallelism": "replicas" if ws > 1 else "single GPU",
                       "l2": "inputs larger than L2 (two 671 MB FP64 state arrays)"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                         "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,

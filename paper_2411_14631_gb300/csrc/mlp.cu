@@ -167,6 +167,22 @@ __device__ __forceinline__ void grad_store(const float acc[][4], float *out, int
     }
 }
 
+// stage the BF16 SiLU activations (as the forward pass computes them) transposed
+__device__ __forceinline__ void stage_T_silu(__nv_bfloat16 (*dst)[TS], const float v[8][4], int w, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t p = silu_bf16x2(v[nt][2 * h], v[nt][2 * h + 1]);
+            const int row = 16 * w + g + (h ? 8 : 0);
+            const int col = nt * 8 + 2 * t;
+            dst[col][row] = *reinterpret_cast<const __nv_bfloat16 *>(&p);
+            dst[col + 1][row] = *(reinterpret_cast<const __nv_bfloat16 *>(&p) + 1);
+        }
+}
+
 // stage an accumulator-layout [16 samples][64] block of warp w as bf16 transposed rows
 template <typename F>
 __device__ __forceinline__ void stage_T(__nv_bfloat16 (*dst)[TS], const float v[8][4], int w, int lane, F f)
@@ -241,7 +257,7 @@ __global__ void __launch_bounds__(256, 1) k_train_grad(const void *packed, const
 #pragma unroll
             for (int i = 0; i < 4; ++i) sm.dzT[i & 1][16 * w + g + (i >= 2 ? 8 : 0)] = __float2bfloat16_rn(dz4[i]);
         }
-        stage_T(sm.aT, z[2], w, lane, silu);
+        stage_T_silu(sm.aT, z[2], w, lane);
         __syncthreads();
         grad_gemm<4>(sm, g4, w, lane);
         {
@@ -267,7 +283,7 @@ __global__ void __launch_bounds__(256, 1) k_train_grad(const void *packed, const
                 for (int i = 0; i < 4; ++i) v8[nt][i] *= dsilu(zl[nt][i]);
             __syncthreads();
             stage_T(sm.dzT, v8, w, lane, [](float q) { return q; });
-            stage_T(sm.aT, z[L - 2], w, lane, silu);
+            stage_T_silu(sm.aT, z[L - 2], w, lane);
             __syncthreads();
             if (L == 3) grad_gemm<3>(sm, g3, w, lane);
             else grad_gemm<2>(sm, g2, w, lane);

@@ -67,11 +67,29 @@ __device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU(z) = z sigma(z) = (z/2) (1 + tanh(z/2)): one hardware tanh per value.  The hidden
+// activations are computed on BF16 pairs (they are BF16 A fragments of the next layer
+// anyway); the backward pass uses the FP32 derivative sigma (1 + z (1 - sigma)).
+__device__ __forceinline__ float tanh_approx(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float silu(float z) { return 0.5f * z * (1.0f + tanh_approx(0.5f * z)); }
 __device__ __forceinline__ float dsilu(float z)
 {
-    const float s = 1.0f / (1.0f + __expf(-z));
+    const float s = 0.5f + 0.5f * tanh_approx(0.5f * z);
     return s * (1.0f + z * (1.0f - s));
+}
+// two SiLUs on a BF16 pair: h = z/2, silu = h + h tanh(h)
+__device__ __forceinline__ uint32_t silu_bf16x2(float z0, float z1)
+{
+    const uint32_t h = pack_bf16(0.5f * z0, 0.5f * z1);
+    uint32_t t, r;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
+    asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(r) : "r"(h), "r"(t));
+    return r;
 }
 
 // B fragment of a row-major [N][stride] weight block for n-tile nt, k-tile kt
@@ -82,6 +100,18 @@ __device__ __forceinline__ void bfrag(const __nv_bfloat16 *W, int stride, int nt
     const __nv_bfloat16 *row = W + (nt * 8 + g) * stride + kt * 16 + 2 * t;
     b0 = ld32(row);
     b1 = ld32(row + 8);
+}
+
+// accumulator n-tiles (2kt, 2kt+1) -> A fragment k-tile kt through SiLU on BF16 pairs
+__device__ __forceinline__ void acc_to_a_silu(const float acc[8][4], uint32_t a[4][4])
+{
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+        a[kt][0] = silu_bf16x2(acc[2 * kt][0], acc[2 * kt][1]);
+        a[kt][1] = silu_bf16x2(acc[2 * kt][2], acc[2 * kt][3]);
+        a[kt][2] = silu_bf16x2(acc[2 * kt + 1][0], acc[2 * kt + 1][1]);
+        a[kt][3] = silu_bf16x2(acc[2 * kt + 1][2], acc[2 * kt + 1][3]);
+    }
 }
 
 // accumulator n-tiles (2kt, 2kt+1) -> A fragment k-tile kt, with an elementwise map
@@ -164,7 +194,7 @@ __device__ __forceinline__ void forward16(const Packed &P, const float *x16, int
 #pragma unroll
                 for (int i = 0; i < 4; ++i) z[layer][nt][i] = acc[nt][i];
         }
-        acc_to_a(acc, a, silu);
+        acc_to_a_silu(acc, a);
         hidden64(a, P.w + (layer == 0 ? PW2 : PW3), P.b + H * (layer + 1), acc, lane);
     }
     if (z) {
@@ -173,7 +203,7 @@ __device__ __forceinline__ void forward16(const Packed &P, const float *x16, int
 #pragma unroll
             for (int i = 0; i < 4; ++i) z[2][nt][i] = acc[nt][i];
     }
-    acc_to_a(acc, a, silu);
+    acc_to_a_silu(acc, a);
     const int t = lane & 3;
     float o[4] = {P.b[3 * H + 2 * t], P.b[3 * H + 2 * t + 1], P.b[3 * H + 2 * t], P.b[3 * H + 2 * t + 1]};
 #pragma unroll

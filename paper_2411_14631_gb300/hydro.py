@@ -216,7 +216,8 @@ class Simulation:
 
     Each ``step()`` is one pass of the hot path: Godunov update of every level (one
     launch), reflux + restriction from the finest level up, and the CFL step of the next
-    step fused into both (dt never leaves the device)."""
+    step fused into both (dt never leaves the device).  With ``use_graph()`` the step is
+    replayed from two CUDA graphs (state A -> B and B -> A), captured once."""
 
     def __init__(self, tree, prm, w0=None, u0=None):
         self.tree, self.prm = tree, prm
@@ -235,11 +236,34 @@ class Simulation:
         self.time = 0.0
         self.nsteps = 0
 
+        self._graphs = None
+
     def step(self, stream=None):
-        hydro_step(self.tree, self.prm, self.u, self.u_new, self.reg, self.dt, self.dt_next, stream)
+        if self._graphs is not None:
+            self._graphs[self.nsteps % 2].replay()
+        else:
+            hydro_step(self.tree, self.prm, self.u, self.u_new, self.reg, self.dt, self.dt_next, stream)
         self.u, self.u_new = self.u_new, self.u
         self.dt, self.dt_next = self.dt_next, self.dt
         self.nsteps += 1
+
+    def use_graph(self):
+        """Capture the two step graphs (after one eager step, which sets kernel attributes)."""
+        self.step()
+        torch.cuda.synchronize()
+        graphs = []
+        s = torch.cuda.Stream(device=self.tree.device)
+        bufs = [(self.u, self.u_new, self.dt, self.dt_next), (self.u_new, self.u, self.dt_next, self.dt)]
+        # graph k is used when nsteps % 2 == k; the buffers alternate with every step
+        order = bufs if self.nsteps % 2 == 0 else bufs[::-1]
+        for (a, b, d0, d1) in order:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                hydro_step(self.tree, self.prm, a, b, self.reg, d0, d1, stream=s)
+            graphs.append(g)
+        self._graphs = graphs
+        torch.cuda.synchronize()
+        return self
 
     def prims(self):
         w = torch.empty_like(self.u)

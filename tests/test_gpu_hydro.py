@@ -225,3 +225,34 @@ def test_uniform_flow_preserved(oracle, H):
             sim.step()
         torch.cuda.synchronize()
         assert torch.equal(sim.u, u0)
+
+
+def test_cuda_graph_replay_matches_eager(oracle, H):
+    import torch
+    lx = W.random_tree(3, 2, 61, p_refine=0.3, periodic=True)
+    g = H.Octree(lx, 3, PER)
+    t = oracle.Tree(lx, 3, PER)
+    xyz, _ = t.cell_centres()
+    w0 = _smooth_random(xyz, 12)
+    for precision in (0, 1):
+        a = H.Simulation(g, H.Params(5 / 3, precision=precision), w0=w0)
+        b = H.Simulation(g, H.Params(5 / 3, precision=precision), w0=w0).use_graph()
+        for _ in range(5):
+            a.step()
+        for _ in range(4):
+            b.step()
+        torch.cuda.synchronize()
+        assert torch.equal(a.u, b.u) and torch.equal(a.dt, b.dt)
+
+
+def test_autotuner_picks_a_candidate(oracle, H, tmp_path, monkeypatch):
+    from paper_2411_14631_gb300 import autotune
+    monkeypatch.setenv("AMRHYDRO_TUNE_CACHE", str(tmp_path / "tune.json"))
+    lx = W.uniform_tree(5)
+    g = H.Octree(lx, 5, OUT)
+    t = oracle.Tree(lx, 5, OUT)
+    xyz, _ = t.cell_centres()
+    tile, ms = autotune.tune(g, 1.4, W.sod_prims(xyz), steps=2)
+    assert tile in (1, 2) and set(ms) == {"1", "2"}
+    tile2, ms2 = autotune.tune(g, 1.4, W.sod_prims(xyz), steps=2)   # cached
+    assert tile2 == tile and ms2 == ms

@@ -60,8 +60,12 @@ enum { AMR_PREC_FP64 = 0, AMR_PREC_FP32 = 1 };
 
 /* Mesh description for amr_build_octree. */
 typedef struct {
-    int32_t levelmin;   /* levels 1..levelmin are complete; 2 <= levelmin */
+    int32_t levelmin;   /* levels 1..levelmin are complete; 2 <= levelmin (octree mode) */
     int32_t bc[6];      /* box faces -x,+x,-y,+y,-z,+z: AMR_BC_PERIODIC (both faces of an axis) or AMR_BC_OUTFLOW */
+    int32_t n_inst;     /* 0: one octree from the oct list.  > 0: batch mode, n_inst independent
+                           uniform unit boxes (the oct list is then ignored) */
+    const int32_t *h_inst_n;   /* batch mode: host [n_inst], cells per dimension of each box,
+                                  a multiple of 4 (cubic cells of size 1/N) */
 } amr_geom;
 
 /* Scheme parameters.  gamma: ratio of specific heats; cfl: Courant number of the
@@ -102,8 +106,16 @@ typedef struct {
     uint8_t *fused;                         /* per oct: 1 iff its father cell is restricted inside
                                                hydro_godunov_level (all eight cells leaves, none next
                                                to a refined cell), 0 if hydro_reflux_level does it */
-    int32_t *tile_root[2];                  /* per tile: root oct (level l-d-1) */
+    int32_t *tile_root[2];                  /* per tile: root oct (level l-d-1); batch mode: corner oct */
     int32_t *tile_slot[2];                  /* per tile: (2^(d+1)+2)^3 stencil slots */
+    /* batch mode (n_inst > 0): octs of box i are [inst_oct_off[i], inst_oct_off[i+1]) in
+       lexicographic (ix fastest) order, lvl[oct] holds the box index, no refinement; the
+       time step is per box: d_dt and d_dt_next of the hydro calls are arrays [n_inst]. */
+    int32_t n_inst;
+    int32_t *inst_n;                        /* device [n_inst]: cells per dimension */
+    double *inst_dx;                        /* device [n_inst]: 1 / N */
+    int64_t *inst_oct_off;                  /* device [n_inst + 1] */
+    int32_t *tile_inst[2];                  /* device, per tile: box index (batch mode) */
 } amr_tree;
 
 /* Sizes of the caller buffers amr_build_octree needs for this oct list (host list of
@@ -129,7 +141,8 @@ amr_status hydro_init_from_prim(const amr_tree *tree, const hydro_params *params
 amr_status hydro_prim_of_state(const amr_tree *tree, const hydro_params *params, const double *d_u,
                                double *d_w, amr_stream stream);
 
-/* newdt_fine (Table 1): *d_dt = cfl * min over leaf cells of dx_l / sum_d (|u_d| + c),
+/* newdt_fine (Table 1): *d_dt = cfl * min over leaf cells of dx_l / sum_d (|u_d| + c)
+   (batch mode: d_dt[i] for each box i, over its cells),
    c = sqrt(gamma p / rho).  FP64 for AMR_PREC_FP64; for AMR_PREC_FP32 it is evaluated
    in FP32, rounded to an FP32 value and scaled by (1 - 2^-16) so that it never exceeds
    the FP64 result. */

@@ -18,7 +18,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = ["riemann.c", "tree.c", "hydro.c", "mlp.c"]
+_SRC = ["riemann.c", "tree.c", "hydro.c", "mlp.c", "box.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 OK, EINVAL, EUNBALANCED, ENONPHYSICAL, ENOCONV = 0, -1, -2, -6, -7
@@ -78,6 +78,8 @@ def lib():
         L.or_step.argtypes = [P, P, P, P, P, C.c_int]
         L.or_init_from_prim.argtypes = [P, P, P, P]
         L.or_prim_of_state.argtypes = [P, P, P, P]
+        L.or_box_courant.argtypes = [C.c_int64, P, P, P]
+        L.or_box_step.argtypes = [C.c_int64, P, P, P, P, C.c_double]
         L.or_mlp_nparams.restype = C.c_int64
         L.or_mlp_features.argtypes = [P, P, C.c_double, P, P]
         L.or_mlp_forward.argtypes = [P, P, C.c_int64, P, P]
@@ -248,6 +250,23 @@ def riemann_flux(WL, WR, prm):
     WL = _f64(WL); WR = _f64(WR); F = np.empty(5)
     st = lib().or_riemann_flux(_p(WL), _p(WR), C.byref(prm), _p(F))
     return F, st
+
+
+# ---- uniform boxes ----------------------------------------------------------------
+def box_courant(N, u, prm):
+    u = _f64(u)
+    dt = C.c_double()
+    lib().or_box_courant(N, C.byref(prm), _p(u), C.byref(dt))
+    return dt.value
+
+
+def box_step(N, bc, u, prm, dt):
+    """One step of a uniform N^3 box; state [5][N^3] with cell i + N (j + N k)."""
+    u = _f64(u)
+    un = np.empty_like(u)
+    bc = np.ascontiguousarray(bc, dtype=np.int32)
+    st = lib().or_box_step(N, _p(bc), C.byref(prm), _p(u), _p(un), dt)
+    return un, st
 
 
 # ---- surrogate network ---------------------------------------------------------

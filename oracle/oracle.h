@@ -84,6 +84,10 @@ int or_step(const or_tree *t, const or_params *p, const double *u_old, double *u
 int or_init_from_prim(const or_tree *t, const or_params *p, const double *w, double *u);
 int or_prim_of_state(const or_tree *t, const or_params *p, const double *u, double *w);
 
+/* one uniform box of N^3 cells of size 1/N, state [5][N^3] with cell i + N (j + N k) */
+int or_box_courant(int64_t N, const or_params *p, const double *u, double *dt);
+int or_box_step(int64_t N, const int32_t *bc, const or_params *p, const double *u, double *u_new, double dt);
+
 /* learned Riemann surrogate (FP64 reference of the network) */
 int64_t or_mlp_nparams(void);
 void or_mlp_features(const double *WL, const double *WR, double gamma, double *x /*[7]*/, double *ref /*[3]*/);

@@ -25,7 +25,7 @@ STATIC_REG_MAX_OCTS = 131072
 
 
 class AmrGeom(C.Structure):
-    _fields_ = [("levelmin", C.c_int32), ("bc", C.c_int32 * 6)]
+    _fields_ = [("levelmin", C.c_int32), ("bc", C.c_int32 * 6), ("n_inst", C.c_int32), ("h_inst_n", C.c_void_p)]
 
 
 class HydroParams(C.Structure):
@@ -43,7 +43,8 @@ class AmrTree(C.Structure):
                 ("key", C.c_void_p), ("son", C.c_void_p), ("father", C.c_void_p), ("nbor", C.c_void_p),
                 ("nb27", C.c_void_p), ("refmask", C.c_void_p), ("fused", C.c_void_p),
                 ("tile_root", C.c_void_p * 2),
-                ("tile_slot", C.c_void_p * 2)]
+                ("tile_slot", C.c_void_p * 2), ("n_inst", C.c_int32), ("inst_n", C.c_void_p), ("inst_dx", C.c_void_p),
+                ("inst_oct_off", C.c_void_p), ("tile_inst", C.c_void_p * 2)]
 
 
 _lib = None

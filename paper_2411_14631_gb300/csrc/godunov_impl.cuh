@@ -35,6 +35,7 @@ template <int D> struct Geo {
 struct GArgs {
     TreeView tv;
     const int32_t *tile_root, *tile_slot;
+    const int32_t *tile_inst;    // batch mode: box of each tile (dt, dt_next are per box)
     int64_t tile_off[AMR_MAXLEV + 2];
     int64_t t_begin, t_end;
     int32_t lfirst, llast;                 // levels covered by [t_begin, t_end)
@@ -305,7 +306,6 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
     static_assert(3 * NV * G::NF <= NV * G::NC, "flux buffer must fit in the stencil buffer");
     const TreeView &tv = a.tv;
     const int tid = threadIdx.x;
-    const double dt = *a.dt;
     Prm<R> pr;
     pr.gamma = to_work<R>(a.gamma); pr.rho_floor = to_work<R>(a.rho_floor); pr.p_floor = to_work<R>(a.p_floor);
     const R cflR = to_work<R>(a.cfl);
@@ -313,17 +313,34 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
     unsigned n_acc = 0, n_fb = 0;   // surrogate: accepted faces, fallbacks (counted by lane 0)
     for (int64_t t = a.t_begin + blockIdx.x; t < a.t_end; t += gridDim.x) {
         // ---- level of this tile and its geometry
-        int l = a.lfirst;
-        while (l < a.llast && t >= a.tile_off[l + 1]) ++l;
         const int32_t root = a.tile_root[t];
-        const int64_t n = int64_t(1) << l;                      // cells per dimension at level l
-        // a depth-D root covers 2^(D+1) level-l cells per axis; stencil index 0 is two cells before
-        const int64_t X0[3] = {int64_t(tv.ix[root]) * (2 << D) - 2, int64_t(tv.iy[root]) * (2 << D) - 2,
-                               int64_t(tv.iz[root]) * (2 << D) - 2};
-        const double dx = pow2(-l);
-        const double lam = scale_pow2(dt, l);    // dt / dx, exact
+        int l = a.lfirst;
+        int64_t n;                   // cells per dimension of the tile's level (or box)
+        double dx, lam;              // cell size, dt / dx
+        double *dtn;                 // where the next step's CFL candidates go
+        int64_t X0[3];               // global cell coordinates of stencil index 0
+        if (a.tile_inst) {
+            // batch mode: a box of N^3 cells of size 1/N, its own time step; the root is
+            // the tile's corner oct
+            const int b = a.tile_inst[t];
+            n = tv.inst_n[b];
+            dx = tv.inst_dx[b];
+            lam = a.dt[b] * double(n);
+            dtn = a.dt_next ? a.dt_next + b : nullptr;
+            X0[0] = 2 * int64_t(tv.ix[root]) - 2; X0[1] = 2 * int64_t(tv.iy[root]) - 2; X0[2] = 2 * int64_t(tv.iz[root]) - 2;
+        } else {
+            while (l < a.llast && t >= a.tile_off[l + 1]) ++l;
+            n = int64_t(1) << l;
+            // a depth-D root covers 2^(D+1) level-l cells per axis; stencil index 0 is two cells before
+            X0[0] = int64_t(tv.ix[root]) * (2 << D) - 2;
+            X0[1] = int64_t(tv.iy[root]) * (2 << D) - 2;
+            X0[2] = int64_t(tv.iz[root]) * (2 << D) - 2;
+            dx = pow2(-l);
+            lam = scale_pow2(*a.dt, l);    // dt / dx, exact
+            dtn = a.dt_next;
+        }
         int mine_out = 0;
-        const bool finer = l < tv.levelmax;   // only then can a stencil cell be refined
+        const bool finer = !a.tile_inst && l < tv.levelmax;   // only then can a stencil cell be refined
         for (int s = tid; s < G::NSLOT; s += blockDim.x) {
             const int32_t e = a.tile_slot[t * G::NSLOT + s];
             sm.slot[s] = e;
@@ -470,15 +487,15 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
 #pragma unroll
                 for (int v = 0; v < NV; ++v) sU[v][q] = Un[v];   // kept for the restriction pass
             }
-            if (a.dt_next && !nbref) {
+            if (dtn && !nbref) {
                 // CFL candidate (newdt_fine) from the final new state of this leaf cell
                 const double cand = cfl_candidate<R>(Un, pr, cflR, to_work<R>(dx));
                 my_dt = umin64(my_dt, dbits(cand));
             }
         }
-        if (a.dt_next) {
+        if (dtn) {
             for (int off = 16; off > 0; off >>= 1) my_dt = umin64(my_dt, __shfl_xor_sync(0xffffffffu, my_dt, off));
-            if ((tid & 31) == 0 && my_dt != ~0ull) atomicMin(reinterpret_cast<unsigned long long *>(a.dt_next), my_dt);
+            if ((tid & 31) == 0 && my_dt != ~0ull) atomicMin(reinterpret_cast<unsigned long long *>(dtn), my_dt);
         }
 
         // ---- restriction of father cells whose eight children are final here: one thread per
@@ -548,9 +565,39 @@ template <typename R>
 amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, const double *u_old, double *u_new,
                          double *reg, const double *dt, double *dt_next, cudaStream_t st)
 {
-    const int depth = p->tile == 0 ? 1 : p->tile;
+    int depth = p->tile == 0 ? 1 : p->tile;
     if (depth != 1 && depth != 2) return AMR_EINVAL;
     if (depth == 2 && sizeof(R) == 8) return AMR_EINVAL;   // an FP64 12^3-cell stencil does not fit in smem
+    if (t->n_inst > 0) {
+        // batch mode: every tile of every box in one launch
+        if (level != -1) return AMR_EINVAL;
+        if (depth == 2 && t->tile_off[1][1] == 0) depth = 1;            // some box is not a multiple of 8
+        if (p->riemann == AMR_RIEMANN_MLP) depth = 1;
+        const int d = depth;
+        GArgs a;
+        a.tv = make_view(t);
+        a.tile_root = t->tile_root[d - 1];
+        a.tile_slot = t->tile_slot[d - 1];
+        a.tile_inst = t->tile_inst[d - 1];
+        for (int i = 0; i < AMR_MAXLEV + 2; ++i) a.tile_off[i] = t->tile_off[d - 1][i];
+        a.lfirst = a.llast = 0;
+        a.t_begin = 0;
+        a.t_end = t->tile_off[d - 1][1];
+        a.u_old = u_old; a.u_new = u_new; a.reg = nullptr; a.dt = dt; a.dt_next = dt_next;
+        a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
+        a.status = p->d_status; a.counters = p->d_counters;
+        a.mlp = p->mlp_weights; a.mlp_tol = p->mlp_resid_tol;
+        a.harvest = nullptr; a.harvest_cap = 0; a.harvest_stride = 1; a.harvest_count = nullptr;
+        const int64_t nt = a.t_end;
+        constexpr int D2 = 2 - (sizeof(R) == 8);
+        if (p->riemann == AMR_RIEMANN_MLP) {
+            if (sizeof(R) == 8 || !p->mlp_weights) return AMR_EINVAL;
+            return launch<R, 1, AMR_RIEMANN_MLP>(a, nt, st);
+        }
+        if (p->riemann == AMR_RIEMANN_EXACT)
+            return d == 1 ? launch<R, 1, AMR_RIEMANN_EXACT>(a, nt, st) : launch<R, D2, AMR_RIEMANN_EXACT>(a, nt, st);
+        return d == 1 ? launch<R, 1, AMR_RIEMANN_HLLC>(a, nt, st) : launch<R, D2, AMR_RIEMANN_HLLC>(a, nt, st);
+    }
     const int l0 = level < 0 ? t->levelmin : level, l1 = level < 0 ? t->levelmax : level;
     if (l0 < t->levelmin || l1 > t->levelmax) return AMR_EINVAL;
     int lsplit = l0;
@@ -563,6 +610,7 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
         a.tv = make_view(t);
         a.tile_root = t->tile_root[d - 1];
         a.tile_slot = t->tile_slot[d - 1];
+        a.tile_inst = nullptr;
         for (int i = 0; i < AMR_MAXLEV + 2; ++i) a.tile_off[i] = t->tile_off[d - 1][i];
         a.lfirst = la;
         a.llast = lb;
@@ -610,6 +658,7 @@ inline amr_status harvest_impl(const amr_tree *t, const hydro_params *p, const d
     a.tv = make_view(t);
     a.tile_root = t->tile_root[0];
     a.tile_slot = t->tile_slot[0];
+    a.tile_inst = nullptr;
     for (int i = 0; i < AMR_MAXLEV + 2; ++i) a.tile_off[i] = t->tile_off[0][i];
     a.lfirst = t->levelmin;
     a.llast = t->levelmax;

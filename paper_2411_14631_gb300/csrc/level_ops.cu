@@ -40,6 +40,28 @@ __global__ void k_courant(TreeView tv, int64_t cell0, const double *__restrict__
     min_to(dt, cand);
 }
 
+// batch mode: per-box CFL step (box cell ranges are multiples of 64, so a warp never
+// straddles two boxes)
+template <typename R>
+__global__ void k_courant_batch(TreeView tv, const double *__restrict__ u, double gamma, double rf, double pf,
+                                double cfl, double *dt)
+{
+    const int64_t cell = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    double cand = DBL_MAX;
+    int b = 0;
+    if (cell < tv.ncell) {
+        b = tv.lvl[cell >> 3];
+        double U[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = u[v * tv.ncell + cell];
+        Prm<R> p;
+        p.gamma = to_work<R>(gamma); p.rho_floor = to_work<R>(rf); p.p_floor = to_work<R>(pf);
+        cand = cfl_candidate<R>(U, p, to_work<R>(cfl), to_work<R>(tv.inst_dx[b]));
+    }
+    b = __shfl_sync(0xffffffffu, b, 0);
+    min_to(dt + b, cand);
+}
+
 // Coarse level l: leaf cells next to a refined cell take the fine fluxes from the
 // register (-/+ dt/dx * 1/4 * sum of the four fine fluxes); refined cells become the
 // mean of their eight children.
@@ -201,8 +223,18 @@ extern "C" amr_status hydro_courant(const amr_tree *t, const hydro_params *p, co
 {
     if (check(t, p) != AMR_OK || !d_u || !d_dt) return AMR_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    AMR_CUDA_TRY(cudaMemsetAsync(d_dt, 0x7F, sizeof(double), st));
     const TreeView tv = make_view(t);
+    if (t->n_inst > 0) {
+        AMR_CUDA_TRY(cudaMemsetAsync(d_dt, 0x7F, sizeof(double) * size_t(t->n_inst), st));
+        const unsigned nb = unsigned((8 * t->noct + 255) / 256);
+        if (p->precision == AMR_PREC_FP32)
+            k_courant_batch<float><<<nb, 256, 0, st>>>(tv, d_u, p->gamma, p->rho_floor, p->p_floor, p->cfl, d_dt);
+        else
+            k_courant_batch<double><<<nb, 256, 0, st>>>(tv, d_u, p->gamma, p->rho_floor, p->p_floor, p->cfl, d_dt);
+        AMR_CUDA_TRY(cudaGetLastError());
+        return AMR_OK;
+    }
+    AMR_CUDA_TRY(cudaMemsetAsync(d_dt, 0x7F, sizeof(double), st));
     const int64_t c0 = t->lvl_off[t->levelmin] * 8, nc = 8 * t->noct - c0;
     const unsigned nb = unsigned((nc + 255) / 256);
     if (p->precision == AMR_PREC_FP32)
@@ -239,7 +271,9 @@ extern "C" amr_status hydro_reflux_level(const amr_tree *t, int level, const hyd
 extern "C" amr_status hydro_step(const amr_tree *t, const hydro_params *p, const double *d_u_old, double *d_u_new,
                                  double *d_flux_reg, const double *d_dt, double *d_dt_next, amr_stream stream)
 {
-    if (d_dt_next) AMR_CUDA_TRY(cudaMemsetAsync(d_dt_next, 0x7F, sizeof(double), reinterpret_cast<cudaStream_t>(stream)));
+    if (d_dt_next)
+        AMR_CUDA_TRY(cudaMemsetAsync(d_dt_next, 0x7F, sizeof(double) * size_t(t && t->n_inst > 0 ? t->n_inst : 1),
+                                     reinterpret_cast<cudaStream_t>(stream)));
     amr_status r = hydro_godunov_level(t, -1, p, d_u_old, d_u_new, d_flux_reg, d_dt, d_dt_next, stream);
     if (r != AMR_OK) return r;
     for (int l = t->levelmax - 1; l >= 1; --l) {
@@ -280,6 +314,7 @@ extern "C" amr_status hydro_harvest_faces(const amr_tree *t, const hydro_params 
 {
     if (check(t, p) != AMR_OK || !d_u || !d_dt || !d_states || !d_count || capacity < 0 || stride < 1)
         return AMR_EINVAL;
+    if (t->n_inst > 0) return AMR_EINVAL;   // octree runs only
     return harvest_dispatch(t, p, d_u, d_dt, d_states, capacity, stride, d_count,
                             reinterpret_cast<cudaStream_t>(stream));
 }

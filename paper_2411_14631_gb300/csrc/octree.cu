@@ -281,6 +281,159 @@ __global__ void k_tile_slots(BuildView b, int depth, int64_t ntile, const int32_
     slot[gi] = v;
 }
 
+// ---- batch mode: independent uniform boxes -------------------------------------------
+struct BoxLayout {
+    size_t lvl, ix, iy, iz, refmask, fused, inst_n, inst_dx, inst_oct_off, root[2], slot[2], tinst[2], total;
+    int64_t noct, ntile[2];
+};
+
+static amr_status box_counts(const amr_geom *g, int64_t *noct, int64_t ntile[2])
+{
+    if (!g->h_inst_n || g->n_inst <= 0 || g->n_inst > (1 << 20)) return AMR_EINVAL;
+    int64_t n = 0, t1 = 0, t2 = 0;
+    bool d2 = true;
+    for (int i = 0; i < g->n_inst; ++i) {
+        const int64_t N = g->h_inst_n[i];
+        if (N < 4 || N % 4 || N > (1 << 16)) return AMR_EINVAL;
+        n += (N / 2) * (N / 2) * (N / 2);
+        t1 += (N / 4) * (N / 4) * (N / 4);
+        if (N % 8) d2 = false; else t2 += (N / 8) * (N / 8) * (N / 8);
+    }
+    if (n > (int64_t(1) << 27)) return AMR_EINVAL;
+    *noct = n;
+    ntile[0] = t1;
+    ntile[1] = d2 ? t2 : 0;
+    return AMR_OK;
+}
+
+static BoxLayout box_layout(const amr_geom *g, int64_t n, const int64_t nt[2])
+{
+    BoxLayout L;
+    L.noct = n; L.ntile[0] = nt[0]; L.ntile[1] = nt[1];
+    size_t o = 0;
+    auto put = [&](size_t bytes) { size_t at = o; o += al256(bytes); return at; };
+    L.lvl = put(4 * n); L.ix = put(4 * n); L.iy = put(4 * n); L.iz = put(4 * n);
+    L.refmask = put(n); L.fused = put(n);
+    L.inst_n = put(4 * size_t(g->n_inst)); L.inst_dx = put(8 * size_t(g->n_inst));
+    L.inst_oct_off = put(8 * (size_t(g->n_inst) + 1));
+    for (int d = 0; d < 2; ++d) {
+        L.root[d] = put(4 * nt[d]);
+        L.slot[d] = put(4 * nt[d] * nslot(d + 1));
+        L.tinst[d] = put(4 * nt[d]);
+    }
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ int find_box(const int64_t *off, int n_inst, int64_t i)
+{
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_box_octs(int n_inst, const int64_t *__restrict__ off, const int32_t *__restrict__ N, int64_t n,
+                           int32_t *lvl, int32_t *ix, int32_t *iy, int32_t *iz, uint8_t *refmask, uint8_t *fused)
+{
+    const int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (o >= n) return;
+    const int b = find_box(off, n_inst, o);
+    const int64_t M = N[b] / 2, j = o - off[b];
+    lvl[o] = b;
+    ix[o] = int32_t(j % M);
+    iy[o] = int32_t((j / M) % M);
+    iz[o] = int32_t(j / (M * M));
+    refmask[o] = 0;
+    fused[o] = 0;
+}
+
+// tiles of depth d: 2^d octs per axis; tile_off[b] = first tile of box b
+__global__ void k_box_tiles(int n_inst, const int64_t *__restrict__ toff, const int64_t *__restrict__ ooff,
+                            const int32_t *__restrict__ N, int depth, int64_t ntile, const int32_t *bc,
+                            int32_t *root, int32_t *tinst, int32_t *slot)
+{
+    const int ns = (1 << depth) + 2, nsl = ns * ns * ns;
+    const int64_t gi = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (gi >= ntile * nsl) return;
+    const int64_t t = gi / nsl;
+    const int s = int(gi % nsl);
+    const int b = find_box(toff, n_inst, t);
+    const int64_t M = N[b] / 2, T = M >> depth, j = t - toff[b];
+    const int64_t c[3] = {(j % T) << depth, ((j / T) % T) << depth, (j / (T * T)) << depth};
+    if (s == 0) {
+        root[t] = int32_t(ooff[b] + c[0] + M * (c[1] + M * c[2]));
+        tinst[t] = b;
+    }
+    int64_t P[3] = {c[0] - 1 + s % ns, c[1] - 1 + (s / ns) % ns, c[2] - 1 + s / (ns * ns)};
+    int out = 0;
+    for (int a = 0; a < 3; ++a) out |= bc_apply(bc, a, M, P[a]);
+    slot[gi] = out ? OUTSIDE : int32_t(ooff[b] + P[0] + M * (P[1] + M * P[2]));
+}
+
+static amr_status build_boxes(const amr_geom *g, void *d_tree_mem, size_t tree_bytes, void *d_ws, size_t ws_bytes,
+                              amr_tree *out, cudaStream_t st)
+{
+    int64_t n, nt[2];
+    if (box_counts(g, &n, nt) != AMR_OK) return AMR_EINVAL;
+    const BoxLayout L = box_layout(g, n, nt);
+    const size_t wsz = al256(8 * (size_t(g->n_inst) + 1)) * 3 + 256;
+    if (tree_bytes < L.total || ws_bytes < wsz) return AMR_ECAPACITY;
+    char *T = static_cast<char *>(d_tree_mem), *S = static_cast<char *>(d_ws);
+    std::memset(out, 0, sizeof(*out));
+    out->noct = n;
+    for (int f = 0; f < 6; ++f) out->bc[f] = g->bc[f];
+    for (int l = 1; l < AMR_MAXLEV + 2; ++l) out->lvl_off[l] = n;
+    out->reg_base = n;
+    out->lvl = (int32_t *)(T + L.lvl); out->ix = (int32_t *)(T + L.ix); out->iy = (int32_t *)(T + L.iy);
+    out->iz = (int32_t *)(T + L.iz); out->refmask = (uint8_t *)(T + L.refmask); out->fused = (uint8_t *)(T + L.fused);
+    out->n_inst = g->n_inst;
+    out->inst_n = (int32_t *)(T + L.inst_n);
+    out->inst_dx = (double *)(T + L.inst_dx);
+    out->inst_oct_off = (int64_t *)(T + L.inst_oct_off);
+    std::vector<int64_t> ooff(g->n_inst + 1), toff[2];
+    std::vector<double> dx(g->n_inst);
+    toff[0].resize(g->n_inst + 1); toff[1].resize(g->n_inst + 1);
+    ooff[0] = toff[0][0] = toff[1][0] = 0;
+    for (int i = 0; i < g->n_inst; ++i) {
+        const int64_t N = g->h_inst_n[i];
+        ooff[i + 1] = ooff[i] + (N / 2) * (N / 2) * (N / 2);
+        toff[0][i + 1] = toff[0][i] + (N / 4) * (N / 4) * (N / 4);
+        toff[1][i + 1] = toff[1][i] + (nt[1] ? (N / 8) * (N / 8) * (N / 8) : 0);
+        dx[i] = 1.0 / double(N);
+    }
+    int64_t *t0 = (int64_t *)S, *t1 = (int64_t *)(S + al256(8 * (size_t(g->n_inst) + 1)));
+    int32_t *dbc = (int32_t *)(S + 2 * al256(8 * (size_t(g->n_inst) + 1)));
+    AMR_CUDA_TRY(cudaMemcpyAsync(out->inst_n, g->h_inst_n, 4 * size_t(g->n_inst), cudaMemcpyHostToDevice, st));
+    AMR_CUDA_TRY(cudaMemcpyAsync(out->inst_dx, dx.data(), 8 * size_t(g->n_inst), cudaMemcpyHostToDevice, st));
+    AMR_CUDA_TRY(cudaMemcpyAsync(out->inst_oct_off, ooff.data(), 8 * ooff.size(), cudaMemcpyHostToDevice, st));
+    AMR_CUDA_TRY(cudaMemcpyAsync(t0, toff[0].data(), 8 * toff[0].size(), cudaMemcpyHostToDevice, st));
+    AMR_CUDA_TRY(cudaMemcpyAsync(t1, toff[1].data(), 8 * toff[1].size(), cudaMemcpyHostToDevice, st));
+    AMR_CUDA_TRY(cudaMemcpyAsync(dbc, g->bc, 6 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const int TB = 256;
+    k_box_octs<<<unsigned((n + TB - 1) / TB), TB, 0, st>>>(g->n_inst, out->inst_oct_off, out->inst_n, n, out->lvl,
+                                                           out->ix, out->iy, out->iz, out->refmask, out->fused);
+    for (int d = 0; d < 2; ++d) {
+        out->tile_root[d] = (int32_t *)(T + L.root[d]);
+        out->tile_slot[d] = (int32_t *)(T + L.slot[d]);
+        out->tile_inst[d] = (int32_t *)(T + L.tinst[d]);
+        out->tile_off[d][0] = 0;
+        for (int l = 1; l < AMR_MAXLEV + 2; ++l) out->tile_off[d][l] = nt[d];
+        if (nt[d] > 0) {
+            const int64_t tot = nt[d] * nslot(d + 1);
+            k_box_tiles<<<unsigned((tot + TB - 1) / TB), TB, 0, st>>>(g->n_inst, d == 0 ? t0 : t1, out->inst_oct_off,
+                                                                     out->inst_n, d + 1, nt[d], dbc,
+                                                                     out->tile_root[d], out->tile_inst[d],
+                                                                     out->tile_slot[d]);
+        }
+    }
+    AMR_CUDA_TRY(cudaStreamSynchronize(st));
+    AMR_CUDA_TRY(cudaGetLastError());
+    return AMR_OK;
+}
+
 }  // namespace amr
 
 using namespace amr;
@@ -288,6 +441,16 @@ using namespace amr;
 extern "C" amr_status amr_build_octree_query(const amr_geom *geom, const int32_t *h_oct_lxyz, int64_t n_oct,
                                              size_t *tree_bytes, size_t *workspace_bytes)
 {
+    if (geom && geom->n_inst > 0) {
+        if (!tree_bytes || !workspace_bytes) return AMR_EINVAL;
+        for (int f = 0; f < 6; ++f)
+            if (geom->bc[f] != AMR_BC_PERIODIC && geom->bc[f] != AMR_BC_OUTFLOW) return AMR_EINVAL;
+        int64_t n, nt[2];
+        if (box_counts(geom, &n, nt) != AMR_OK) return AMR_EINVAL;
+        *tree_bytes = box_layout(geom, n, nt).total;
+        *workspace_bytes = al256(8 * (size_t(geom->n_inst) + 1)) * 3 + 256;
+        return AMR_OK;
+    }
     if (check_geom(geom, n_oct) != AMR_OK || !h_oct_lxyz || !tree_bytes || !workspace_bytes) return AMR_EINVAL;
     int64_t cnt[AMR_MAXLEV + 2];
     int lmax;
@@ -301,6 +464,16 @@ extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oc
                                        void *d_tree_mem, size_t tree_bytes, void *d_workspace,
                                        size_t workspace_bytes, amr_tree *out, amr_stream stream)
 {
+    if (geom && geom->n_inst > 0) {
+        if (!d_tree_mem || !d_workspace || !out) return AMR_EINVAL;
+        for (int f = 0; f < 6; ++f)
+            if (geom->bc[f] != AMR_BC_PERIODIC && geom->bc[f] != AMR_BC_OUTFLOW) return AMR_EINVAL;
+        for (int a = 0; a < 3; ++a)
+            if ((geom->bc[2 * a] == AMR_BC_PERIODIC) != (geom->bc[2 * a + 1] == AMR_BC_PERIODIC)) return AMR_EINVAL;
+        if ((uintptr_t(d_tree_mem) & 255) || (uintptr_t(d_workspace) & 255)) return AMR_EINVAL;
+        return build_boxes(geom, d_tree_mem, tree_bytes, d_workspace, workspace_bytes, out,
+                           reinterpret_cast<cudaStream_t>(stream));
+    }
     if (check_geom(geom, n) != AMR_OK || !h_oct_lxyz || !d_tree_mem || !d_workspace || !out) return AMR_EINVAL;
     if ((uintptr_t(d_tree_mem) & 255) || (uintptr_t(d_workspace) & 255)) return AMR_EINVAL;
     int64_t cnt[AMR_MAXLEV + 2];

@@ -41,6 +41,32 @@ class Octree:
         self.levelmin, self.levelmax = int(self.t.levelmin), int(self.t.levelmax)
         self.lvl_off = np.array(self.t.lvl_off[:], dtype=np.int64)
 
+    @classmethod
+    def boxes(cls, sizes, bc=(abi.BC_OUTFLOW,) * 6, device="cuda:0", stream=None):
+        """Batch mode: independent uniform unit boxes of sizes[i]^3 cells (multiples of 4)."""
+        self = cls.__new__(cls)
+        sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+        self.device = torch.device(device)
+        g = abi.AmrGeom(0, (C.c_int32 * 6)(*bc), sizes.size, sizes.ctypes.data_as(C.c_void_p))
+        tb, wb = C.c_size_t(), C.c_size_t()
+        check("amr_build_octree_query", lib().amr_build_octree_query(C.byref(g), None, 0, C.byref(tb), C.byref(wb)))
+        self.mem = torch.empty(tb.value, dtype=torch.uint8, device=self.device)
+        ws = torch.empty(wb.value, dtype=torch.uint8, device=self.device)
+        self.t = abi.AmrTree()
+        check("amr_build_octree", lib().amr_build_octree(C.byref(g), None, 0, _ptr(self.mem), tb.value, _ptr(ws),
+                                                         wb.value, C.byref(self.t), _stream(stream)))
+        self.noct = int(self.t.noct)
+        self.ncell = 8 * self.noct
+        self.levelmin = self.levelmax = 0
+        self.lvl_off = np.array(self.t.lvl_off[:], dtype=np.int64)
+        self.sizes = sizes
+        self.cell_off = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 3)])
+        return self
+
+    @property
+    def n_inst(self):
+        return int(self.t.n_inst)
+
     def _view(self, ptr, n, dtype):
         off = ptr - self.mem.data_ptr()
         nbytes = n * torch.tensor([], dtype=dtype).element_size()
@@ -60,6 +86,8 @@ class Octree:
         return int(self.t.tile_off[depth - 1][abi.MAXLEV + 1])
 
     def leaf_cells(self):
+        if self.t.n_inst > 0:
+            return self.ncell
         return int((self.tables()["son"] < 0).sum())
 
     def flux_reg_bytes(self):
@@ -225,8 +253,9 @@ class Simulation:
         self.u = torch.empty((5, tree.ncell), dtype=torch.float64, device=dev)
         self.u_new = torch.empty_like(self.u)
         self.reg = torch.zeros(max(1, tree.flux_reg_bytes() // 8), dtype=torch.float64, device=dev)
-        self.dt = torch.zeros(1, dtype=torch.float64, device=dev)
-        self.dt_next = torch.zeros(1, dtype=torch.float64, device=dev)
+        ndt = max(1, int(tree.t.n_inst))          # batch mode: one time step per box
+        self.dt = torch.zeros(ndt, dtype=torch.float64, device=dev)
+        self.dt_next = torch.zeros(ndt, dtype=torch.float64, device=dev)
         if u0 is not None:
             self.u.copy_(u0)
         else:

@@ -239,3 +239,49 @@ def sedov_prims(xyz, level, e_blast=1.0, rho=1.0, p=1e-5, gamma=1.4):
 
 
 SOD_GAMMA, TURB_GAMMA, PLUMMER_GAMMA, SEDOV_GAMMA = 1.4, 5.0 / 3.0, 5.0 / 3.0, 1.4
+
+
+# ---- batches of independent uniform boxes ------------------------------------------
+def sedov_batch_sizes(n=48, seed=5, lo=32, hi=192, step=16):
+    """n box sizes drawn uniformly from {lo, lo+step, ..., hi} with default_rng(seed)."""
+    choices = np.arange(lo, hi + 1, step)
+    return np.random.default_rng(seed).choice(choices, size=n).astype(np.int32)
+
+
+def box_cell_ijk(N):
+    """(i, j, k) of every cell of one N^3 box in the batch layout: octs lexicographic
+    (x fastest), cell c = cx + 2 cy + 4 cz inside the oct."""
+    M = N // 2
+    o = np.arange(M ** 3)
+    ox, oy, oz = o % M, (o // M) % M, o // (M * M)
+    c = np.arange(8)
+    i = (2 * ox[:, None] + (c & 1)).ravel()
+    j = (2 * oy[:, None] + ((c >> 1) & 1)).ravel()
+    k = (2 * oz[:, None] + ((c >> 2) & 1)).ravel()
+    return i, j, k
+
+
+def box_batch_to_lex(N):
+    """Index array: position in the batch layout -> lexicographic index i + N (j + N k)."""
+    i, j, k = box_cell_ijk(N)
+    return i + N * (j + N * k)
+
+
+def sedov_box_prims_lex(N, e_blast=1.0, rho=1.0, p=1e-5, gamma=1.4):
+    """Sedov data for one N^3 box in lexicographic order: the blast energy, as pressure,
+    in cell (N/2, N/2, N/2)."""
+    W = np.zeros((5, N ** 3))
+    W[0] = rho
+    W[4] = p
+    c = N // 2
+    W[4, c + N * (c + N * c)] = p + (gamma - 1.0) * e_blast * N ** 3
+    return W
+
+
+def batch_prims(sizes, per_box_lex):
+    """Concatenate per-box lexicographic fields into the batch layout."""
+    out = []
+    for N in sizes:
+        W = per_box_lex(int(N))
+        out.append(W[:, box_batch_to_lex(int(N))])
+    return np.concatenate(out, axis=1)

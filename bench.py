@@ -390,6 +390,81 @@ def study_surrogate(args):
     return 0
 
 
+def study_sedov(args):
+    """Batch of 48 independent Sedov-Taylor blasts on uneven boxes (32^3..192^3, sizes from
+    default_rng(5)), one launch per step with a CFL step per box.  Throughput of the chosen
+    FP32 path and the plain FP64 path (CUDA graphs); then each box runs until its exact
+    shock radius reaches 0.3 (frozen afterwards by a zero time step) and its numerical
+    radius (peak of the radially averaged density) is compared with R = xi0 (E t^2/rho)^(1/5),
+    xi0 = 0.851^(-1/5) for gamma = 1.4 (Kamm & Timmes 2007)."""
+    import numpy as np
+    import torch
+    from paper_2411_14631_gb300 import build, abi
+    build.build()
+    from paper_2411_14631_gb300 import hydro as H
+    from paper_2411_14631_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    sizes = W.sedov_batch_sizes(48, seed=5)
+    tree = H.Octree.boxes(sizes, (abi.BC_OUTFLOW,) * 6)
+    w0 = W.batch_prims(sizes, lambda N: W.sedov_box_prims_lex(N))
+    cells = tree.ncell
+    out = {"study": "Sedov-Taylor batch: 48 boxes, one launch per step, per-box CFL", "data": "synthetic",
+           "sizes": [int(x) for x in sizes], "cells": cells}
+    from paper_2411_14631_gb300 import autotune
+    tile, tune_ms = autotune.tune(tree, 1.4, w0, precision=abi.PREC_FP32, cfl=CFL, use_cache=False)
+    res = {}
+    for name, prec, steps in (("fp32_chosen", abi.PREC_FP32, args.steps), ("fp64_plain", abi.PREC_FP64, 3)):
+        prm = H.Params(1.4, cfl=CFL, precision=prec, tile=tile if prec == abi.PREC_FP32 else 1)
+        ms, _ = time_graph(H, tree, prm, w0, steps, 2)
+        res[name] = {"ms_per_step": ms, "cell_updates_per_s": cells / (ms * 1e-3), "steps_timed": steps}
+    res["speedup"] = res["fp64_plain"]["ms_per_step"] / res["fp32_chosen"]["ms_per_step"]
+    out["throughput"] = res
+    out["tile_depth"] = tile
+    out["autotune_ms_per_step"] = tune_ms
+    # accuracy run: FP32 chosen path, each box frozen at its own target radius
+    xi0 = 0.851 ** -0.2
+    prm = H.Params(1.4, cfl=CFL, precision=abi.PREC_FP32, tile=tile)
+    sim = H.Simulation(tree, prm, w0=w0)
+    tb = np.zeros(len(sizes))
+    frozen = np.zeros(len(sizes), dtype=bool)
+    nstep = 0
+    while not frozen.all() and nstep < 5000:
+        d = sim.dt.cpu().numpy()
+        d[frozen] = 0.0
+        # freeze a box when its next step would pass the target time
+        t_target = (0.3 / xi0) ** 2.5
+        over = (~frozen) & (tb + d > t_target)
+        d[over] = np.maximum(t_target - tb[over], 0.0)
+        sim.dt.copy_(torch.as_tensor(d))
+        tb += d
+        frozen |= over
+        sim.step()
+        nstep += 1
+    rho = sim.u[0].cpu().numpy()
+    radii = []
+    for b, N in enumerate(sizes):
+        N = int(N)
+        i, j, k = W.box_cell_ijk(N)
+        seg = rho[tree.cell_off[b]:tree.cell_off[b + 1]]
+        c = (N // 2 + 0.5) / N
+        r = np.sqrt(((i + 0.5) / N - c) ** 2 + ((j + 0.5) / N - c) ** 2 + ((k + 0.5) / N - c) ** 2)
+        nb = int(0.5 * N)
+        idx = np.minimum((r * N).astype(np.int64), nb)
+        sums = np.bincount(idx, weights=seg, minlength=nb + 1)[:nb]
+        cnts = np.bincount(idx, minlength=nb + 1)[:nb]
+        prof = sums / np.maximum(cnts, 1)
+        R_num = (np.argmax(prof) + 0.5) / N
+        R_ex = xi0 * (tb[b] ** 2) ** 0.2
+        radii.append({"N": N, "t": float(tb[b]), "R_exact": R_ex, "R_num": R_num,
+                      "rel_err": abs(R_num - R_ex) / R_ex, "ok": bool(abs(R_num - R_ex) <= max(2.0 / N, 0.05 * R_ex))})
+    out["accuracy"] = {"steps": nstep, "all_within_max(2 cells, 5%)": all(r["ok"] for r in radii),
+                       "max_rel_err": max(r["rel_err"] for r in radii), "per_box": radii}
+    st, _ = prm.read_status()
+    out["device_status"] = st
+    print(json.dumps(out))
+    return 0
+
+
 def leaf_count(tree):
     return tree.leaf_cells()
 
@@ -404,7 +479,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=["surrogate"])
+    ap.add_argument("--study", default=None, choices=["surrogate", "sedov"])
     ap.add_argument("--harvest", type=int, default=10_000_000)
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--tol", type=float, default=0.02)
@@ -412,6 +487,8 @@ def main():
     ws, rank, local = dist_setup()
     if args.study == "surrogate":
         return study_surrogate(args)
+    if args.study == "sedov":
+        return study_sedov(args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
 

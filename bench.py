@@ -465,6 +465,59 @@ def study_sedov(args):
     return 0
 
 
+def study_amr(args):
+    """Plummer-clump AMR mesh (base level 7 refined to level 12, 64 clumps): throughput of
+    the chosen FP32 path and the plain FP64 path (all levels in one update launch, then
+    reflux + restriction per level, CUDA graphs), and conservation over 10 steps."""
+    import numpy as np
+    import torch
+    from paper_2411_14631_gb300 import build, abi
+    build.build()
+    from paper_2411_14631_gb300 import hydro as H
+    from paper_2411_14631_gb300 import workloads as W
+    from paper_2411_14631_gb300.bench_util import cell_centres_of
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    lx, centres = W.plummer_tree()
+    tree = H.Octree(lx, 7, (abi.BC_PERIODIC,) * 6)
+    w0 = W.plummer_prims(cell_centres_of(tree), centres)
+    tab = tree.tables()
+    son = tab["son"].cpu().numpy()
+    lvl = np.repeat(tab["lvl"].cpu().numpy(), 8)
+    leaf = son < 0
+    out = {"study": "Plummer-clump AMR mesh, levels 7-12, all levels in one launch", "data": "synthetic",
+           "octs": tree.noct, "leaf_cells": int(leaf.sum()),
+           "leaf_cells_per_level": {int(l): int((leaf & (lvl == l)).sum()) for l in range(7, 13)},
+           "setup_seconds": time.perf_counter() - t0}
+    from paper_2411_14631_gb300 import autotune
+    tile, tune_ms = autotune.tune(tree, 5.0 / 3.0, w0, precision=abi.PREC_FP32, cfl=CFL, use_cache=False)
+    res = {}
+    for name, prec, steps in (("fp32_chosen", abi.PREC_FP32, args.steps), ("fp64_plain", abi.PREC_FP64, 3)):
+        prm = H.Params(5.0 / 3.0, cfl=CFL, precision=prec, tile=tile if prec == abi.PREC_FP32 else 1)
+        ms, sim = time_graph(H, tree, prm, w0, steps, 2)
+        res[name] = {"ms_per_step": ms, "cell_updates_per_s": int(leaf.sum()) / (ms * 1e-3), "steps_timed": steps}
+    res["speedup"] = res["fp64_plain"]["ms_per_step"] / res["fp32_chosen"]["ms_per_step"]
+    out["throughput"] = res
+    out["tile_depth"] = tile
+    out["autotune_ms_per_step"] = tune_ms
+    vol = np.ldexp(1.0, -3 * lvl.astype(np.int64))[leaf]
+    for name, prec in (("fp64", abi.PREC_FP64), ("fp32", abi.PREC_FP32)):
+        sim = H.Simulation(tree, H.Params(5.0 / 3.0, cfl=CFL, precision=prec, tile=tile if prec else 1), w0=w0)
+        u0 = sim.u.cpu().numpy()
+        tot0 = np.array([np.sum(u0[v, leaf] * vol) for v in range(5)])
+        for _ in range(10):
+            sim.step()
+        u1 = sim.u.cpu().numpy()
+        tot1 = np.array([np.sum(u1[v, leaf] * vol) for v in range(5)])
+        # drift of each total relative to the larger of its start and end absolute sums
+        # (momenta start at zero)
+        scale = np.array([max(np.sum(np.abs(u0[v, leaf]) * vol), np.sum(np.abs(u1[v, leaf]) * vol))
+                          for v in range(5)])
+        out["conservation_" + name] = {"steps": 10, "rel_drift": [float(x) for x in np.abs(tot1 - tot0) / scale]}
+    print(json.dumps(out))
+    return 0
+
+
 def leaf_count(tree):
     return tree.leaf_cells()
 
@@ -479,7 +532,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=["surrogate", "sedov"])
+    ap.add_argument("--study", default=None, choices=["surrogate", "sedov", "amr"])
     ap.add_argument("--harvest", type=int, default=10_000_000)
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--tol", type=float, default=0.02)
@@ -489,6 +542,8 @@ def main():
         return study_surrogate(args)
     if args.study == "sedov":
         return study_sedov(args)
+    if args.study == "amr":
+        return study_amr(args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
 

@@ -73,8 +73,10 @@ __device__ __forceinline__ int64_t coarse_neighbour(const TreeView &tv, int64_t 
     return so >= 0 ? int64_t(so) * 8 + cc : int64_t(N);
 }
 
-// child c of coarse leaf cell F: U_F + sum_d s_d/4 minmod(U_F - U_{F-e_d}, U_{F+e_d} - U_F)
-static __device__ void interp_child(const TreeView &tv, const double *__restrict__ u, int64_t F, int c, double out[NV])
+// child c of coarse leaf cell F: U_F + sum_d s_d/4 minmod(U_F - U_{F-e_d}, U_{F+e_d} - U_F),
+// on conserved variables in the working precision R (FP64 values read from the state)
+template <typename R>
+__device__ void interp_child(const TreeView &tv, const double *__restrict__ u, int64_t F, int c, R out[NV])
 {
     const int64_t oF = F >> 3;
     const int cf = int(F & 7);
@@ -89,15 +91,27 @@ static __device__ void interp_child(const TreeView &tv, const double *__restrict
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        const double uc = u[v * tv.ncell + F];
-        double r = uc;
+        const R uc = to_work<R>(u[v * tv.ncell + F]);
+        R r = uc;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const double m = minmod(uc - u[v * tv.ncell + nm[d]], u[v * tv.ncell + np[d]] - uc);
-            r = r + (((c >> d) & 1) ? 0.25 * m : -0.25 * m);
+            const R m = minmod(uc - to_work<R>(u[v * tv.ncell + nm[d]]), to_work<R>(u[v * tv.ncell + np[d]]) - uc);
+            r = r + (((c >> d) & 1) ? R(0.25) * m : -R(0.25) * m);
         }
         out[v] = r;
     }
+}
+
+// cons -> prim from conserved values already in the working precision
+template <typename R>
+__device__ __forceinline__ void cons_to_prim_w(const R U[NV], const Prm<R> &p, R W[NV])
+{
+    const R rho = rmax(U[0], p.rho_floor);
+    const R u = U[1] / rho, v = U[2] / rho, w = U[3] / rho;
+    const R ek = R(0.5) * rho * (u * u + v * v + w * w);
+    const R pr = (p.gamma - R(1)) * (U[4] - ek);
+    W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
+    W[4] = rmax(pr, p.p_floor);
 }
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
@@ -357,17 +371,17 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
             const int si = i + G::C * (j + G::C * k);
             const int32_t e = sm.slot[s];
             if (e == OUTSIDE) continue;
-            double U[NV];
+            R Uw[NV];
             if (e >= 0) {
 #pragma unroll
-                for (int v = 0; v < NV; ++v) U[v] = a.u_old[v * tv.ncell + int64_t(e) * 8 + c];
+                for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(a.u_old[v * tv.ncell + int64_t(e) * 8 + c]);
             } else if (e == UNNEEDED_SLOT) {
-                U[0] = 1.0; U[1] = 0.0; U[2] = 0.0; U[3] = 0.0; U[4] = 1.0;
+                Uw[0] = R(1); Uw[1] = R(0); Uw[2] = R(0); Uw[3] = R(0); Uw[4] = R(1);
             } else {
-                interp_child(tv, a.u_old, int64_t(-1) - e, c, U);
+                interp_child<R>(tv, a.u_old, int64_t(-1) - e, c, Uw);
             }
             R Wc[NV];
-            cons_to_prim(U, pr, Wc);
+            cons_to_prim_w(Uw, pr, Wc);
 #pragma unroll
             for (int v = 0; v < NV; ++v) sm.W[v][si] = Wc[v];
         }

@@ -134,7 +134,7 @@ def grf(n, seed, slope=-4.0):
     amp = np.zeros_like(k2)
     nz = k2 > 0
     amp[nz] = k2[nz] ** (slope / 4.0)            # sqrt(P) = k^(slope/2)
-    d = np.fft.irfftn(f * amp, s=(n, n, n))
+    d = np.fft.irfftn(f * amp, s=(n, n, n), axes=(0, 1, 2))
     d -= d.mean()
     return d / d.std()
 
@@ -190,30 +190,39 @@ def plummer_density(xyz, centres, a=PLUMMER_A, contrast=PLUMMER_CONTRAST, chunk=
 def plummer_tree(base=7, lmax=12, nclump=64, seed=3):
     """Base level complete; a level-l cell (base <= l < lmax) is refined iff
     rho * dx_l^3 > dx_base^3 (a mass threshold of one background base cell, i.e.
-    rho > 8^(l-base)), strict; then 2:1 balanced (periodic)."""
+    rho > 8^(l-base)), strict; then 2:1 balanced (periodic).  Above the base level only
+    cells within the radius where one clump alone could pass the threshold are examined
+    (the other clumps and the background add less than 2 there)."""
     centres = plummer_centres(nclump, seed)
     levels = {l: full_level(l) for l in range(1, base + 1)}
-    cur = levels[base]
+    cur = levels[base]                      # octs of level l (packed coordinates)
     a, K = PLUMMER_A, PLUMMER_CONTRAST
     for l in range(base, lmax):
         thr = 8.0 ** (l - base)
-        x, y, z = _unpack(cur)
-        kids = []
-        for c in range(8):
-            cx, cy, cz = 2 * x + (c & 1), 2 * y + ((c >> 1) & 1), 2 * z + ((c >> 2) & 1)
-            if l > base:
-                # only cells where one clump alone could pass: other clumps add < 1
-                rcut2 = a * a * ((K / max(thr - 2.0, 1e-30)) ** 0.4 - 1.0)
-                xyz = (np.stack([cx, cy, cz], axis=1) + 0.5) * np.ldexp(1.0, -l)
-                d = xyz[:, None, :] - centres[None]
-                d -= np.round(d)
-                near = (np.einsum("ijk,ijk->ij", d, d) <= rcut2).any(axis=1)
-                cx, cy, cz = cx[near], cy[near], cz[near]
-            xyz = (np.stack([cx, cy, cz], axis=1) + 0.5) * np.ldexp(1.0, -l)
-            rho = plummer_density(xyz, centres)
-            pick = rho > thr
-            kids.append(_pack(cx[pick], cy[pick], cz[pick]))
-        cur = np.unique(np.concatenate(kids))
+        n = 1 << l                          # cells per dimension at level l
+        if l == base:
+            x, y, z = _unpack(cur)
+            c = np.arange(8)
+            cx = (2 * x[:, None] + (c & 1)).ravel()
+            cy = (2 * y[:, None] + ((c >> 1) & 1)).ravel()
+            cz = (2 * z[:, None] + ((c >> 2) & 1)).ravel()
+        else:
+            rcut = a * np.sqrt((K / (thr - 2.0)) ** 0.4 - 1.0)
+            R = int(np.ceil(rcut * n)) + 1
+            off = np.arange(-R, R + 1)
+            ox, oy, oz = np.meshgrid(off, off, off, indexing="ij")
+            cand = []
+            for cen in centres:
+                ic = np.floor(cen * n).astype(np.int64)
+                cand.append(_pack((ic[0] + ox.ravel()) % n, (ic[1] + oy.ravel()) % n, (ic[2] + oz.ravel()) % n))
+            cells = np.unique(np.concatenate(cand))
+            cx, cy, cz = _unpack(cells)
+            inside = np.isin(_pack(cx >> 1, cy >> 1, cz >> 1), cur)   # the cell exists (its oct does)
+            cx, cy, cz = cx[inside], cy[inside], cz[inside]
+        xyz = (np.stack([cx, cy, cz], axis=1) + 0.5) / n
+        rho = plummer_density(xyz, centres)
+        pick = rho > thr
+        cur = np.unique(_pack(cx[pick], cy[pick], cz[pick]))   # refined cells = octs of level l+1
         if cur.size == 0:
             break
         levels[l + 1] = cur

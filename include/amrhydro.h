@@ -73,6 +73,8 @@ typedef struct {
    riemann: AMR_RIEMANN_*; precision: AMR_PREC_FP64 (all arithmetic in FP64) or
    AMR_PREC_FP32 (reconstruction and Riemann solve in FP32, state accumulation in FP64);
    tile: 1 or 2 = depth of the oct tiles a CTA updates (8 or 64 octs), 0 = default;
+   tiles_only: 0 = a complete finest level (uniform, nothing refined) is updated by the
+   z-column kernel (same arithmetic per cell, less ghost work), 1 = tiles for every level;
    mlp_weights: device pointer to the surrogate's weights (AMR_RIEMANN_MLP only);
    mlp_resid_tol: acceptance threshold of the surrogate's residual check;
    d_status: device int32 error word (may be NULL); d_counters: device uint64
@@ -80,7 +82,7 @@ typedef struct {
    [1] surrogate fallbacks to the exact solver, [2] exact-solver failures. */
 typedef struct {
     double gamma, cfl, rho_floor, p_floor;
-    int32_t riemann, precision, tile, reserved;
+    int32_t riemann, precision, tile, tiles_only;
     const void *mlp_weights;
     float mlp_resid_tol, reserved_f;
     int32_t *d_status;
@@ -116,6 +118,10 @@ typedef struct {
     double *inst_dx;                        /* device [n_inst]: 1 / N */
     int64_t *inst_oct_off;                  /* device [n_inst + 1] */
     int32_t *tile_inst[2];                  /* device, per tile: box index (batch mode) */
+    /* octree mode, when the finest level is complete: grid[ix + M (iy + M iz)] = oct index of
+       that level (M = 2^(grid_level-1)), used by the z-column kernel; grid_level = 0 if none */
+    int32_t grid_level;
+    int32_t *grid;
 } amr_tree;
 
 /* Sizes of the caller buffers amr_build_octree needs for this oct list (host list of

@@ -30,7 +30,7 @@ class AmrGeom(C.Structure):
 
 class HydroParams(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("rho_floor", C.c_double), ("p_floor", C.c_double),
-                ("riemann", C.c_int32), ("precision", C.c_int32), ("tile", C.c_int32), ("reserved", C.c_int32),
+                ("riemann", C.c_int32), ("precision", C.c_int32), ("tile", C.c_int32), ("tiles_only", C.c_int32),
                 ("mlp_weights", C.c_void_p), ("mlp_resid_tol", C.c_float), ("reserved_f", C.c_float),
                 ("d_status", C.c_void_p), ("d_counters", C.c_void_p)]
 
@@ -44,7 +44,8 @@ class AmrTree(C.Structure):
                 ("nb27", C.c_void_p), ("refmask", C.c_void_p), ("fused", C.c_void_p),
                 ("tile_root", C.c_void_p * 2),
                 ("tile_slot", C.c_void_p * 2), ("n_inst", C.c_int32), ("inst_n", C.c_void_p), ("inst_dx", C.c_void_p),
-                ("inst_oct_off", C.c_void_p), ("tile_inst", C.c_void_p * 2)]
+                ("inst_oct_off", C.c_void_p), ("tile_inst", C.c_void_p * 2), ("grid_level", C.c_int32),
+                ("grid", C.c_void_p)]
 
 
 _lib = None

@@ -1,0 +1,305 @@
+// godunov_fine on a complete finest level: the z-column ("2.5D") form of the update.
+//
+// When the finest level l is complete (2^(l-1) octs per axis, nothing refined) the level
+// is a uniform grid; a CTA owns an FX x FY-cell footprint and marches a ZC-cell segment
+// of its column in z, two cell planes (one oct layer) per slab, keeping rings of
+//   W  -- primitive stencil planes (live: the slab's planes - 2 .. + 3),
+//   Q  -- predicted planes (W~ and the three MinMod slopes; live: -1 .. +2),
+//   Fz -- z-face fluxes (the face below each live plane),
+// so every stencil plane is gathered, predicted and every z face solved once per
+// segment; only the x-y halo is repeated.  Per cell the arithmetic is the tile kernel's,
+// in the same order (gather conversion, predictor, face states, Riemann solve, flux sum
+// x-left, x-right, y-left, y-right, z-below, z-above, FP64 update, CFL candidate,
+// restriction), so the two kernels give bitwise equal states.
+#pragma once
+#include "hydro_math.cuh"
+
+namespace amr {
+
+template <typename R, int FX, int FY> struct ColSmem {
+    static constexpr int SX = FX + 4, SY = FY + 4;   // stencil footprint (cells)
+    static constexpr int PX = FX + 2, PY = FY + 2;   // predicted footprint
+    R W[8][NV][SY * SX];                             // ring, slot = plane & 7
+    R Q[4][4 * NV][PY * PX];                         // ring, slot = plane & 3
+    R Fx[2][NV][FY * (FX + 1)];                      // x faces of the slab's two planes
+    R Fy[2][NV][(FY + 1) * FX];
+    R Fz[4][NV][FY * FX];                            // face below plane j, slot j & 3
+    double U[NV][2 * FY * FX];                       // new states of the slab
+    int32_t cell[2 * FY * FX];                       // their cell ids (oct*8 + c)
+};
+
+struct ColArgs {
+    TreeView tv;
+    const int32_t *grid;
+    int level;
+    int64_t n;              // cells per dimension
+    int zc;                 // segment length in cells (multiple of 2, divides n)
+    const double *u_old;
+    double *u_new;
+    const double *dt;
+    double *dt_next;
+    double gamma, rho_floor, p_floor, cfl;
+    int32_t *status;
+};
+
+// Riemann flux in the face-normal frame (HLLC, or the exact solver with HLLC fallback)
+template <typename R, int RS>
+__device__ __forceinline__ void col_solve(const R WL[NV], const R WR[NV], const Prm<R> &pr, int32_t *status,
+                                          R Fn[NV])
+{
+    if (RS == AMR_RIEMANN_EXACT) {
+        R ps, us;
+        const R tol = sizeof(R) == 8 ? R(1e-14) : R(1e-6);
+        const int e = exact_star(WL, WR, pr.gamma, tol, 50, ps, us);
+        if (e == 0) {
+            R W0[NV], U0[NV];
+            exact_sample0(WL, WR, pr.gamma, ps, us, W0);
+            flux_normal(W0, pr.gamma, Fn, U0);
+        } else {
+            set_error(status, e);
+            hllc(WL, WR, pr.gamma, Fn);
+        }
+    } else {
+        hllc(WL, WR, pr.gamma, Fn);
+    }
+}
+
+// face between predicted cells pl (left) and pr_ (right) of rings QL, QR along DIR
+template <typename R, int DIR, int PXY>
+__device__ __forceinline__ void col_face(const R (*QL)[PXY], const R (*QR)[PXY], int pl, int pr_, const Prm<R> &pr,
+                                         R WL[NV], R WR[NV])
+{
+    constexpr int N0 = DIR + 1, T1 = DIR == 0 ? 2 : 1, T2 = DIR == 2 ? 2 : 3;
+    constexpr int S = NV + NV * DIR;
+    WL[0] = QL[0][pl] + R(0.5) * QL[S + 0][pl];
+    WR[0] = QR[0][pr_] - R(0.5) * QR[S + 0][pr_];
+    WL[1] = QL[N0][pl] + R(0.5) * QL[S + N0][pl];
+    WR[1] = QR[N0][pr_] - R(0.5) * QR[S + N0][pr_];
+    WL[2] = QL[T1][pl] + R(0.5) * QL[S + T1][pl];
+    WR[2] = QR[T1][pr_] - R(0.5) * QR[S + T1][pr_];
+    WL[3] = QL[T2][pl] + R(0.5) * QL[S + T2][pl];
+    WR[3] = QR[T2][pr_] - R(0.5) * QR[S + T2][pr_];
+    WL[4] = QL[4][pl] + R(0.5) * QL[S + 4][pl];
+    WR[4] = QR[4][pr_] - R(0.5) * QR[S + 4][pr_];
+    WL[0] = rmax(WL[0], pr.rho_floor); WR[0] = rmax(WR[0], pr.rho_floor);
+    WL[4] = rmax(WL[4], pr.p_floor); WR[4] = rmax(WR[4], pr.p_floor);
+}
+
+template <int DIR, typename R, int N>
+__device__ __forceinline__ void col_store(R (*F)[N], int r, const R Fn[NV])
+{
+    constexpr int N0 = DIR + 1, T1 = DIR == 0 ? 2 : 1, T2 = DIR == 2 ? 2 : 3;
+    F[0][r] = Fn[0];
+    F[N0][r] = Fn[1];
+    F[T1][r] = Fn[2];
+    F[T2][r] = Fn[3];
+    F[4][r] = Fn[4];
+}
+
+template <typename R, int RS, int FX, int FY>
+__global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
+{
+    using S = ColSmem<R, FX, FY>;
+    constexpr int SX = S::SX, SY = S::SY, PX = S::PX, PY = S::PY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S &sm = *reinterpret_cast<S *>(smem_raw);
+    const TreeView &tv = a.tv;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    Prm<R> pr;
+    pr.gamma = to_work<R>(a.gamma); pr.rho_floor = to_work<R>(a.rho_floor); pr.p_floor = to_work<R>(a.p_floor);
+    const R cflR = to_work<R>(a.cfl);
+    const int l = a.level;
+    const int64_t n = a.n, M = n / 2;
+    const double dx = pow2(-l);
+    const double lam = scale_pow2(*a.dt, l);     // dt / dx, exact
+    const R lamR = to_work<R>(lam);
+    const R hl = R(0.5) * lamR;
+    const R dxR = to_work<R>(dx);
+    const bool per[3] = {tv.bc[0] == AMR_BC_PERIODIC, tv.bc[2] == AMR_BC_PERIODIC, tv.bc[4] == AMR_BC_PERIODIC};
+    const int64_t nfx = n / FX, nfy = n / FY, nseg = n / a.zc;
+    unsigned long long my_dt = ~0ull;
+
+    auto wrap = [&](int64_t c, int axis) -> int64_t {
+        if (c >= 0 && c < n) return c;
+        if (per[axis]) return (c + n) % n;
+        return c < 0 ? 0 : n - 1;                  // outflow: clamp at this level
+    };
+    auto cell_id = [&](int64_t X, int64_t Y, int64_t Z) -> int64_t {
+        const int64_t o = a.grid[(X >> 1) + M * ((Y >> 1) + M * (Z >> 1))];
+        return o * 8 + (X & 1) + 2 * (Y & 1) + 4 * (Z & 1);
+    };
+
+    for (int64_t b = blockIdx.x; b < nfx * nfy * nseg; b += gridDim.x) {
+        const int64_t fxy = b % (nfx * nfy), seg = b / (nfx * nfy);
+        const int64_t X0 = (fxy % nfx) * FX - 2, Y0 = (fxy / nfx) * FY - 2;   // stencil index 0
+        const int64_t z0 = seg * a.zc;
+
+        // gather oct layer L (cell planes 2L, 2L+1) of the stencil footprint
+        auto gather = [&](int64_t L) {
+            for (int q = tid; q < (SX / 2) * (SY / 2) * 8; q += nt) {
+                const int o = q >> 3, c = q & 7;
+                const int i = 2 * (o % (SX / 2)) + (c & 1), j = 2 * (o / (SX / 2)) + ((c >> 1) & 1);
+                const int64_t zp = 2 * L + ((c >> 2) & 1);
+                const int64_t cid = cell_id(wrap(X0 + i, 0), wrap(Y0 + j, 1), wrap(zp, 2));
+                R Uw[NV], Wc[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(a.u_old[v * tv.ncell + cid]);
+                cons_to_prim_w(Uw, pr, Wc);
+                const int slot = int(zp & 7);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sm.W[slot][v][i + SX * j] = Wc[v];
+            }
+        };
+        // MinMod slopes + MUSCL-Hancock predictor of plane p (cells 1..SX-2 x 1..SY-2)
+        auto predict = [&](int64_t p) {
+            const int s0 = int(p & 7), sm1 = int((p - 1) & 7), sp1 = int((p + 1) & 7), qs = int(p & 3);
+            for (int r = tid; r < PX * PY; r += nt) {
+                const int i = 1 + r % PX, j = 1 + r / PX;
+                const int si = i + SX * j;
+                R Wc[NV], Dl[3][NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) Wc[v] = sm.W[s0][v][si];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    Dl[0][v] = minmod(Wc[v] - sm.W[s0][v][si - 1], sm.W[s0][v][si + 1] - Wc[v]);
+                    Dl[1][v] = minmod(Wc[v] - sm.W[s0][v][si - SX], sm.W[s0][v][si + SX] - Wc[v]);
+                    Dl[2][v] = minmod(Wc[v] - sm.W[sm1][v][si], sm.W[sp1][v][si] - Wc[v]);
+                }
+                const R rr = Wc[0], u = Wc[1], vv = Wc[2], w = Wc[3], pp = Wc[4];
+                R Wt[NV];
+                Wt[0] = rr - hl * (u * Dl[0][0] + rr * Dl[0][1] + vv * Dl[1][0] + rr * Dl[1][2] + w * Dl[2][0] + rr * Dl[2][3]);
+                Wt[1] = u - hl * (u * Dl[0][1] + vv * Dl[1][1] + w * Dl[2][1] + Dl[0][4] / rr);
+                Wt[2] = vv - hl * (u * Dl[0][2] + vv * Dl[1][2] + w * Dl[2][2] + Dl[1][4] / rr);
+                Wt[3] = w - hl * (u * Dl[0][3] + vv * Dl[1][3] + w * Dl[2][3] + Dl[2][4] / rr);
+                Wt[4] = pp - hl * (u * Dl[0][4] + vv * Dl[1][4] + w * Dl[2][4] + pr.gamma * pp * (Dl[0][1] + Dl[1][2] + Dl[2][3]));
+                const int pq = (i - 1) + PX * (j - 1);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sm.Q[qs][v][pq] = Wt[v];
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) sm.Q[qs][NV + NV * d + v][pq] = Dl[d][v];
+            }
+        };
+        // z faces below planes j (face j-1 | j), for the listed planes
+        auto zfaces = [&](int64_t j0, int count) {
+            for (int r = tid; r < count * FX * FY; r += nt) {
+                const int64_t j = j0 + r / (FX * FY);
+                const int rr = r % (FX * FY), x = rr % FX, y = rr / FX;
+                const int pq = (1 + x) + PX * (1 + y);
+                R WL[NV], WR[NV], Fn[NV];
+                col_face<R, 2, PX * PY>(sm.Q[(j - 1) & 3], sm.Q[j & 3], pq, pq, pr, WL, WR);
+                col_solve<R, RS>(WL, WR, pr, a.status, Fn);
+                col_store<2>(sm.Fz[j & 3], rr, Fn);
+            }
+        };
+
+        gather(z0 / 2 - 1);
+        gather(z0 / 2);
+        __syncthreads();
+        predict(z0 - 1);
+        predict(z0);
+        __syncthreads();
+        zfaces(z0, 1);
+        for (int64_t k = z0; k < z0 + a.zc; k += 2) {
+            gather(k / 2 + 1);
+            __syncthreads();
+            predict(k + 1);
+            predict(k + 2);
+            __syncthreads();
+            // x and y faces of planes k, k+1; z faces below planes k+1, k+2
+            constexpr int NXF = FY * (FX + 1), NYF = (FY + 1) * FX;
+            for (int r = tid; r < 2 * (NXF + NYF); r += nt) {
+                R WL[NV], WR[NV], Fn[NV];
+                if (r < 2 * NXF) {
+                    const int dz = r / NXF, rr = r % NXF, fa = rr % (FX + 1), row = rr / (FX + 1);
+                    const int pl = fa + PX * (1 + row);
+                    const int qs = int((k + dz) & 3);
+                    col_face<R, 0, PX * PY>(sm.Q[qs], sm.Q[qs], pl, pl + 1, pr, WL, WR);
+                    col_solve<R, RS>(WL, WR, pr, a.status, Fn);
+                    col_store<0>(sm.Fx[dz], rr, Fn);
+                } else {
+                    const int r2 = r - 2 * NXF;
+                    const int dz = r2 / NYF, rr = r2 % NYF, col = rr % FX, fa = rr / FX;
+                    const int pl = (1 + col) + PX * fa;
+                    const int qs = int((k + dz) & 3);
+                    col_face<R, 1, PX * PY>(sm.Q[qs], sm.Q[qs], pl, pl + PX, pr, WL, WR);
+                    col_solve<R, RS>(WL, WR, pr, a.status, Fn);
+                    col_store<1>(sm.Fy[dz], rr, Fn);
+                }
+            }
+            zfaces(k + 1, 2);
+            __syncthreads();
+            // FP64 update of the slab's cells, fused CFL candidate
+            for (int q = tid; q < 2 * FX * FY; q += nt) {
+                const int dz = q / (FX * FY), r = q % (FX * FY), x = r % FX, y = r / FX;
+                const int64_t p = k + dz;
+                R dU[NV] = {0, 0, 0, 0, 0};
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    dU[v] = dU[v] + sm.Fx[dz][v][x + (FX + 1) * y];
+                    dU[v] = dU[v] - sm.Fx[dz][v][x + 1 + (FX + 1) * y];
+                    dU[v] = dU[v] + sm.Fy[dz][v][x + FX * y];
+                    dU[v] = dU[v] - sm.Fy[dz][v][x + FX * (y + 1)];
+                    dU[v] = dU[v] + sm.Fz[p & 3][v][r];
+                    dU[v] = dU[v] - sm.Fz[(p + 1) & 3][v][r];
+                }
+                const int64_t cid = cell_id(X0 + 2 + x, Y0 + 2 + y, p);
+                double Un[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    if (sizeof(R) == 8) Un[v] = a.u_old[v * tv.ncell + cid] + lam * to_state(dU[v]);
+                    else Un[v] = a.u_old[v * tv.ncell + cid] + to_state(lamR * dU[v]);
+                    a.u_new[v * tv.ncell + cid] = Un[v];
+                    sm.U[v][q] = Un[v];
+                }
+                sm.cell[q] = int32_t(cid);
+                if (a.dt_next) my_dt = min(my_dt, (unsigned long long)__double_as_longlong(
+                                                    cfl_candidate<R>(Un, pr, cflR, dxR)));
+            }
+            __syncthreads();
+            // restriction of the fathers of the slab's octs (each oct's eight cells in order)
+            for (int w = tid; w < (FX / 2) * (FY / 2) * NV; w += nt) {
+                const int o = w / NV, v = w % NV, oi = o % (FX / 2), oj = o / (FX / 2);
+                const int q0 = 2 * oi + FX * (2 * oj);
+                const int32_t oct = sm.cell[q0] >> 3;
+                if (!tv.fused[oct]) continue;
+                double acc = 0.0;
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    acc += sm.U[v][q0 + (c & 1) + FX * ((c >> 1) & 1) + FX * FY * ((c >> 2) & 1)];
+                a.u_new[v * tv.ncell + tv.father[oct]] = 0.125 * acc;
+            }
+            __syncthreads();
+        }
+    }
+    if (a.dt_next) {
+        for (int off = 16; off > 0; off >>= 1) my_dt = min(my_dt, __shfl_xor_sync(0xffffffffu, my_dt, off));
+        if ((tid & 31) == 0 && my_dt != ~0ull) atomicMin(reinterpret_cast<unsigned long long *>(a.dt_next), my_dt);
+    }
+}
+
+template <typename R, int RS>
+amr_status launch_col(const amr_tree *t, const hydro_params *p, const double *u_old, double *u_new, const double *dt,
+                      double *dt_next, cudaStream_t st)
+{
+    constexpr int FX = 8, FY = 8;
+    ColArgs a;
+    a.tv = make_view(t);
+    a.grid = t->grid;
+    a.level = t->grid_level;
+    a.n = int64_t(1) << t->grid_level;
+    a.zc = a.n < 32 ? int(a.n) : 32;
+    a.u_old = u_old; a.u_new = u_new; a.dt = dt; a.dt_next = dt_next;
+    a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
+    a.status = p->d_status;
+    const size_t bytes = sizeof(ColSmem<R, FX, FY>);
+    auto kern = k_godunov_col<R, RS, FX, FY>;
+    AMR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+    const int64_t work = (a.n / FX) * (a.n / FY) * (a.n / a.zc);
+    kern<<<unsigned(work < 1048576 ? work : 1048576), 256, bytes, st>>>(a);
+    AMR_CUDA_TRY(cudaGetLastError());
+    return AMR_OK;
+}
+
+}  // namespace amr

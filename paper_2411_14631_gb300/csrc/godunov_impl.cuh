@@ -14,6 +14,7 @@
 #include <cfloat>
 #include "hydro_math.cuh"
 #include "mlp_warp.cuh"
+#include "godunov_col.cuh"
 
 namespace amr {
 
@@ -612,8 +613,18 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
             return d == 1 ? launch<R, 1, AMR_RIEMANN_EXACT>(a, nt, st) : launch<R, D2, AMR_RIEMANN_EXACT>(a, nt, st);
         return d == 1 ? launch<R, 1, AMR_RIEMANN_HLLC>(a, nt, st) : launch<R, D2, AMR_RIEMANN_HLLC>(a, nt, st);
     }
-    const int l0 = level < 0 ? t->levelmin : level, l1 = level < 0 ? t->levelmax : level;
+    int l0 = level < 0 ? t->levelmin : level, l1 = level < 0 ? t->levelmax : level;
     if (l0 < t->levelmin || l1 > t->levelmax) return AMR_EINVAL;
+    // a complete finest level goes to the z-column kernel (bitwise the same per cell)
+    if (!p->tiles_only && p->riemann != AMR_RIEMANN_MLP && t->grid && t->grid_level == t->levelmax &&
+        t->grid_level >= 3 && l1 == t->grid_level) {
+        const amr_status r = p->riemann == AMR_RIEMANN_EXACT
+                                 ? launch_col<R, AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, st)
+                                 : launch_col<R, AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, st);
+        if (r != AMR_OK) return r;
+        l1 = t->grid_level - 1;
+        if (l0 > l1) return AMR_OK;
+    }
     int lsplit = l0;
     while (lsplit <= l1 && lsplit - depth < 1) ++lsplit;
     for (int pass = 0; pass < 2; ++pass) {

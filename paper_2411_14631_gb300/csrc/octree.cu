@@ -15,7 +15,7 @@ constexpr int32_t UNNEEDED = INT32_MIN + 1;
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct TreeLayout {
-    size_t lvl, ix, iy, iz, key, son, father, nbor, nb27, refmask, fused, root[2], slot[2], total;
+    size_t lvl, ix, iy, iz, key, son, father, nbor, nb27, refmask, fused, grid, root[2], slot[2], total;
     int64_t tile_bound[2];
 };
 
@@ -37,6 +37,8 @@ static TreeLayout tree_layout(int64_t n, const int64_t cnt[AMR_MAXLEV + 2], int 
     L.lvl = put(4 * n); L.ix = put(4 * n); L.iy = put(4 * n); L.iz = put(4 * n);
     L.key = put(8 * n); L.son = put(32 * n); L.father = put(4 * n); L.nbor = put(24 * n);
     L.nb27 = put(108 * n); L.refmask = put(n); L.fused = put(n);
+    // dense oct grid of the finest level when it is complete
+    L.grid = put(cnt[lmax] == (int64_t(1) << (3 * (lmax - 1))) ? 4 * cnt[lmax] : 0);
     for (int d = 0; d < 2; ++d) {
         L.root[d] = put(4 * L.tile_bound[d]);
         L.slot[d] = put(4 * L.tile_bound[d] * nslot(d + 1));
@@ -231,6 +233,17 @@ __global__ void k_tile_flags(BuildView b, const int32_t *__restrict__ son, const
         }
     }
     flag[o] = f;
+}
+
+__global__ void k_grid(int64_t o0, int64_t o1, int l, const int32_t *__restrict__ ix, const int32_t *__restrict__ iy,
+                       const int32_t *__restrict__ iz, int32_t *grid)
+{
+    const int64_t o = o0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (o >= o1) return;
+    const int64_t M = int64_t(1) << (l - 1);
+    const int64_t x = ix[o], y = iy[o], z = iz[o];
+    if (x < 0 || y < 0 || z < 0 || x >= M || y >= M || z >= M) return;   // invalid input: reported by k_keys
+    grid[x + M * (y + M * z)] = int32_t(o);
 }
 
 __global__ void k_tile_compact(int64_t n, const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
@@ -531,6 +544,13 @@ extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oc
     bv.lvl = out->lvl; bv.ix = out->ix; bv.iy = out->iy; bv.iz = out->iz; bv.key = out->key;
     k_tables<<<nb, TB, 0, st>>>(bv, out->son, out->father, out->nbor, out->nb27, out->refmask, err);
     k_fused<<<nb, TB, 0, st>>>(bv, out->son, out->nbor, out->refmask, out->fused);
+    if (cnt[lmax] == (int64_t(1) << (3 * (lmax - 1))) && lmax >= lmin) {
+        out->grid_level = lmax;
+        out->grid = (int32_t *)(T + L.grid);
+        const int64_t nl = cnt[lmax];
+        k_grid<<<unsigned((nl + TB - 1) / TB), TB, 0, st>>>(out->lvl_off[lmax], out->lvl_off[lmax + 1], lmax, out->ix,
+                                                            out->iy, out->iz, out->grid);
+    }
 
     for (int d = 0; d < 2; ++d) {
         const int depth = d + 1;

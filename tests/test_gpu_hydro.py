@@ -256,3 +256,28 @@ def test_autotuner_picks_a_candidate(oracle, H, tmp_path, monkeypatch):
     assert tile in (1, 2) and set(ms) == {"1", "2"}
     tile2, ms2 = autotune.tune(g, 1.4, W.sod_prims(xyz), steps=2)   # cached
     assert tile2 == tile and ms2 == ms
+
+
+@pytest.mark.parametrize("level,precision,riemann,bc", [(5, 0, 0, OUT), (5, 1, 0, PER), (6, 1, 0, OUT),
+                                                        (6, 0, 1, PER), (5, 1, 1, OUT)])
+def test_column_kernel_equals_tiles(oracle, H, level, precision, riemann, bc):
+    """A complete finest level is updated by the z-column kernel; the tile kernel
+    (tiles_only) gives the same states and time steps bit for bit."""
+    import torch
+    lx = W.uniform_tree(level)
+    g = H.Octree(lx, level, bc)
+    assert g.t.grid_level == level
+    t = oracle.Tree(lx, level, bc)
+    xyz, _ = t.cell_centres()
+    w0 = _smooth_random(xyz, 40 + level)
+    w0[4, :: 97] += 3.0                    # a few pressure spikes: shocks and rarefactions
+    res = []
+    for tiles_only in (False, True):
+        sim = H.Simulation(g, H.Params(5 / 3, cfl=0.6, precision=precision, riemann=riemann,
+                                       tiles_only=tiles_only), w0=w0)
+        for _ in range(3):
+            sim.step()
+        torch.cuda.synchronize()
+        res.append((sim.u.cpu().numpy(), sim.dt.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])

@@ -2,10 +2,10 @@
 //
 // When the finest level l is complete (2^(l-1) octs per axis, nothing refined) the level
 // is a uniform grid; a CTA owns an FX x FY-cell footprint and marches a ZC-cell segment
-// of its column in z, two cell planes (one oct layer) per slab, keeping rings of
-//   W  -- primitive stencil planes (live: the slab's planes - 2 .. + 3),
-//   Q  -- predicted planes (W~ and the three MinMod slopes; live: -1 .. +2),
-//   Fz -- z-face fluxes (the face below each live plane),
+// of its column in z, two cell planes (one oct layer) per slab k, k+1, keeping rings of
+//   W  -- primitive stencil planes k .. k+3,
+//   Q  -- predicted planes k .. k+2 (W~ and the three MinMod slopes),
+//   Fz -- z-face fluxes below planes k .. k+2,
 // so every stencil plane is gathered, predicted and every z face solved once per
 // segment; only the x-y halo is repeated.  Per cell the arithmetic is the tile kernel's,
 // in the same order (gather conversion, predictor, face states, Riemann solve, flux sum
@@ -19,11 +19,11 @@ namespace amr {
 template <typename R, int FX, int FY> struct ColSmem {
     static constexpr int SX = FX + 4, SY = FY + 4;   // stencil footprint (cells)
     static constexpr int PX = FX + 2, PY = FY + 2;   // predicted footprint
-    R W[8][NV][SY * SX];                             // ring, slot = plane & 7
-    R Q[4][4 * NV][PY * PX];                         // ring, slot = plane & 3
+    R W[4][NV][SY * SX];                             // ring, slot = plane & 3 (live: k .. k+3)
+    R Q[3][4 * NV][PY * PX];                         // ring, slot = (plane + 6) % 3 (live: k .. k+2)
     R Fx[2][NV][FY * (FX + 1)];                      // x faces of the slab's two planes
     R Fy[2][NV][(FY + 1) * FX];
-    R Fz[4][NV][FY * FX];                            // face below plane j, slot j & 3
+    R Fz[3][NV][FY * FX];                            // face below plane j, slot (j + 6) % 3
     double U[NV][2 * FY * FX];                       // new states of the slab
     int32_t cell[2 * FY * FX];                       // their cell ids (oct*8 + c)
 };
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         const int64_t X0 = (fxy % nfx) * FX - 2, Y0 = (fxy / nfx) * FY - 2;   // stencil index 0
         const int64_t z0 = seg * a.zc;
 
-        // gather oct layer L (cell planes 2L, 2L+1) of the stencil footprint
+        // gather oct layer L (cell planes 2L, 2L+1) of the stencil footprint into the W ring
         auto gather = [&](int64_t L) {
             for (int q = tid; q < (SX / 2) * (SY / 2) * 8; q += nt) {
                 const int o = q >> 3, c = q & 7;
@@ -145,14 +145,15 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
 #pragma unroll
                 for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(a.u_old[v * tv.ncell + cid]);
                 cons_to_prim_w(Uw, pr, Wc);
-                const int slot = int(zp & 7);
+                const int slot = int(zp & 3);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) sm.W[slot][v][i + SX * j] = Wc[v];
             }
         };
+        auto q3 = [](int64_t p) { return int((p + 6) % 3); };   // planes start at z0 - 2 >= -2
         // MinMod slopes + MUSCL-Hancock predictor of plane p (cells 1..SX-2 x 1..SY-2)
         auto predict = [&](int64_t p) {
-            const int s0 = int(p & 7), sm1 = int((p - 1) & 7), sp1 = int((p + 1) & 7), qs = int(p & 3);
+            const int s0 = int(p & 3), sm1 = int((p - 1) & 3), sp1 = int((p + 1) & 3), qs = q3(p);
             for (int r = tid; r < PX * PY; r += nt) {
                 const int i = 1 + r % PX, j = 1 + r / PX;
                 const int si = i + SX * j;
@@ -188,9 +189,9 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 const int rr = r % (FX * FY), x = rr % FX, y = rr / FX;
                 const int pq = (1 + x) + PX * (1 + y);
                 R WL[NV], WR[NV], Fn[NV];
-                col_face<R, 2, PX * PY>(sm.Q[(j - 1) & 3], sm.Q[j & 3], pq, pq, pr, WL, WR);
+                col_face<R, 2, PX * PY>(sm.Q[q3(j - 1)], sm.Q[q3(j)], pq, pq, pr, WL, WR);
                 col_solve<R, RS>(WL, WR, pr, a.status, Fn);
-                col_store<2>(sm.Fz[j & 3], rr, Fn);
+                col_store<2>(sm.Fz[q3(j)], rr, Fn);
             }
         };
 
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         __syncthreads();
         zfaces(z0, 1);
         for (int64_t k = z0; k < z0 + a.zc; k += 2) {
-            gather(k / 2 + 1);
+            gather(k / 2 + 1);               // planes k+2, k+3 (slots of the dead planes k-2, k-1)
             __syncthreads();
             predict(k + 1);
             predict(k + 2);
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 if (r < 2 * NXF) {
                     const int dz = r / NXF, rr = r % NXF, fa = rr % (FX + 1), row = rr / (FX + 1);
                     const int pl = fa + PX * (1 + row);
-                    const int qs = int((k + dz) & 3);
+                    const int qs = q3(k + dz);
                     col_face<R, 0, PX * PY>(sm.Q[qs], sm.Q[qs], pl, pl + 1, pr, WL, WR);
                     col_solve<R, RS>(WL, WR, pr, a.status, Fn);
                     col_store<0>(sm.Fx[dz], rr, Fn);
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                     const int r2 = r - 2 * NXF;
                     const int dz = r2 / NYF, rr = r2 % NYF, col = rr % FX, fa = rr / FX;
                     const int pl = (1 + col) + PX * fa;
-                    const int qs = int((k + dz) & 3);
+                    const int qs = q3(k + dz);
                     col_face<R, 1, PX * PY>(sm.Q[qs], sm.Q[qs], pl, pl + PX, pr, WL, WR);
                     col_solve<R, RS>(WL, WR, pr, a.status, Fn);
                     col_store<1>(sm.Fy[dz], rr, Fn);
@@ -241,8 +242,8 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                     dU[v] = dU[v] - sm.Fx[dz][v][x + 1 + (FX + 1) * y];
                     dU[v] = dU[v] + sm.Fy[dz][v][x + FX * y];
                     dU[v] = dU[v] - sm.Fy[dz][v][x + FX * (y + 1)];
-                    dU[v] = dU[v] + sm.Fz[p & 3][v][r];
-                    dU[v] = dU[v] - sm.Fz[(p + 1) & 3][v][r];
+                    dU[v] = dU[v] + sm.Fz[q3(p)][v][r];
+                    dU[v] = dU[v] - sm.Fz[q3(p + 1)][v][r];
                 }
                 const int64_t cid = cell_id(X0 + 2 + x, Y0 + 2 + y, p);
                 double Un[NV];

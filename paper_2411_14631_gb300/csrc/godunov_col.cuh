@@ -24,8 +24,8 @@ template <typename R, int FX, int FY> struct ColSmem {
     R Fx[2][NV][FY * (FX + 1)];                      // x faces of the slab's two planes
     R Fy[2][NV][(FY + 1) * FX];
     R Fz[3][NV][FY * FX];                            // face below plane j, slot (j + 6) % 3
-    double U[NV][2 * FY * FX];                       // new states of the slab
-    int32_t cell[2 * FY * FX];                       // their cell ids (oct*8 + c)
+    double U[2][NV][2 * FY * FX];                    // new states of the last two slabs
+    int32_t cell[2][2 * FY * FX];                    // their cell ids (oct*8 + c)
 };
 
 struct ColArgs {
@@ -195,21 +195,10 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             }
         };
 
-        gather(z0 / 2 - 1);
-        gather(z0 / 2);
-        __syncthreads();
-        predict(z0 - 1);
-        predict(z0);
-        __syncthreads();
-        zfaces(z0, 1);
-        for (int64_t k = z0; k < z0 + a.zc; k += 2) {
-            gather(k / 2 + 1);               // planes k+2, k+3 (slots of the dead planes k-2, k-1)
-            __syncthreads();
-            predict(k + 1);
-            predict(k + 2);
-            __syncthreads();
-            // x and y faces of planes k, k+1; z faces below planes k+1, k+2
-            constexpr int NXF = FY * (FX + 1), NYF = (FY + 1) * FX;
+        constexpr int NXF = FY * (FX + 1), NYF = (FY + 1) * FX;
+        constexpr int NG = (SX / 2) * (SY / 2) * 8, NU = 2 * FX * FY, NR = (FX / 2) * (FY / 2) * NV;
+        // x and y faces of planes k, k+1 and z faces below planes k+1, k+2 (those of slab k)
+        auto slab_faces = [&](int64_t k) {
             for (int r = tid; r < 2 * (NXF + NYF); r += nt) {
                 R WL[NV], WR[NV], Fn[NV];
                 if (r < 2 * NXF) {
@@ -230,49 +219,99 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 }
             }
             zfaces(k + 1, 2);
-            __syncthreads();
-            // FP64 update of the slab's cells, fused CFL candidate
-            for (int q = tid; q < 2 * FX * FY; q += nt) {
-                const int dz = q / (FX * FY), r = q % (FX * FY), x = r % FX, y = r / FX;
-                const int64_t p = k + dz;
-                R dU[NV] = {0, 0, 0, 0, 0};
+        };
+        // FP64 update of cell q of slab k (fused CFL candidate); keeps the new state
+        auto update = [&](int64_t k, int q) {
+            const int dz = q / (FX * FY), r = q % (FX * FY), x = r % FX, y = r / FX;
+            const int64_t p = k + dz;
+            R dU[NV] = {0, 0, 0, 0, 0};
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    dU[v] = dU[v] + sm.Fx[dz][v][x + (FX + 1) * y];
-                    dU[v] = dU[v] - sm.Fx[dz][v][x + 1 + (FX + 1) * y];
-                    dU[v] = dU[v] + sm.Fy[dz][v][x + FX * y];
-                    dU[v] = dU[v] - sm.Fy[dz][v][x + FX * (y + 1)];
-                    dU[v] = dU[v] + sm.Fz[q3(p)][v][r];
-                    dU[v] = dU[v] - sm.Fz[q3(p + 1)][v][r];
-                }
-                const int64_t cid = cell_id(X0 + 2 + x, Y0 + 2 + y, p);
-                double Un[NV];
+            for (int v = 0; v < NV; ++v) {
+                dU[v] = dU[v] + sm.Fx[dz][v][x + (FX + 1) * y];
+                dU[v] = dU[v] - sm.Fx[dz][v][x + 1 + (FX + 1) * y];
+                dU[v] = dU[v] + sm.Fy[dz][v][x + FX * y];
+                dU[v] = dU[v] - sm.Fy[dz][v][x + FX * (y + 1)];
+                dU[v] = dU[v] + sm.Fz[q3(p)][v][r];
+                dU[v] = dU[v] - sm.Fz[q3(p + 1)][v][r];
+            }
+            const int64_t cid = cell_id(X0 + 2 + x, Y0 + 2 + y, p);
+            const int ub = int((k >> 1) & 1);
+            double Un[NV];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    if (sizeof(R) == 8) Un[v] = a.u_old[v * tv.ncell + cid] + lam * to_state(dU[v]);
-                    else Un[v] = a.u_old[v * tv.ncell + cid] + to_state(lamR * dU[v]);
-                    a.u_new[v * tv.ncell + cid] = Un[v];
-                    sm.U[v][q] = Un[v];
+            for (int v = 0; v < NV; ++v) {
+                if (sizeof(R) == 8) Un[v] = a.u_old[v * tv.ncell + cid] + lam * to_state(dU[v]);
+                else Un[v] = a.u_old[v * tv.ncell + cid] + to_state(lamR * dU[v]);
+                a.u_new[v * tv.ncell + cid] = Un[v];
+                sm.U[ub][v][q] = Un[v];
+            }
+            sm.cell[ub][q] = int32_t(cid);
+            if (a.dt_next) my_dt = min(my_dt, (unsigned long long)__double_as_longlong(cfl_candidate<R>(Un, pr, cflR, dxR)));
+        };
+        // restriction of the father of one oct of slab k (its eight cells in order), variable v
+        auto restrict_one = [&](int64_t k, int w) {
+            const int o = w / NV, v = w % NV, oi = o % (FX / 2), oj = o / (FX / 2);
+            const int ub = int((k >> 1) & 1);
+            const int q0 = 2 * oi + FX * (2 * oj);
+            const int32_t oct = sm.cell[ub][q0] >> 3;
+            if (!tv.fused[oct]) return;
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc += sm.U[ub][v][q0 + (c & 1) + FX * ((c >> 1) & 1) + FX * FY * ((c >> 2) & 1)];
+            a.u_new[v * tv.ncell + tv.father[oct]] = 0.125 * acc;
+        };
+
+        // prologue, keeping to the ring sizes (W: 4 planes, Q and Fz: 3): planes z0-2 .. z0+1,
+        // predictions z0-1, z0, the z face below z0 together with planes z0+2, z0+3 (which
+        // replace the dead z0-2, z0-1), predictions z0+1, z0+2 (replacing z0-1), the faces
+        // of slab z0
+        gather(z0 / 2 - 1);
+        gather(z0 / 2);
+        __syncthreads();
+        predict(z0 - 1);
+        predict(z0);
+        __syncthreads();
+        zfaces(z0, 1);
+        gather(z0 / 2 + 1);
+        __syncthreads();
+        predict(z0 + 1);
+        predict(z0 + 2);
+        __syncthreads();
+        slab_faces(z0);
+        __syncthreads();
+        // per slab k: {update of slab k, gather of the layer slab k+2 needs, restriction of
+        // slab k-2} share one phase, then the predictions and faces of slab k+2
+        for (int64_t k = z0; k < z0 + a.zc; k += 2) {
+            const bool more = k + 2 < z0 + a.zc;
+            const int nwork = NU + (more ? NG : 0) + (k > z0 ? NR : 0);
+            for (int w = tid; w < nwork; w += nt) {
+                if (w < NU) {
+                    update(k, w);
+                } else if (more && w < NU + NG) {
+                    const int q = w - NU, o = q >> 3, c = q & 7;
+                    const int i = 2 * (o % (SX / 2)) + (c & 1), j = 2 * (o / (SX / 2)) + ((c >> 1) & 1);
+                    const int64_t zp = k + 4 + ((c >> 2) & 1);
+                    const int64_t cid = cell_id(wrap(X0 + i, 0), wrap(Y0 + j, 1), wrap(zp, 2));
+                    R Uw[NV], Wc[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(a.u_old[v * tv.ncell + cid]);
+                    cons_to_prim_w(Uw, pr, Wc);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) sm.W[int(zp & 3)][v][i + SX * j] = Wc[v];
+                } else {
+                    restrict_one(k - 2, w - NU - (more ? NG : 0));
                 }
-                sm.cell[q] = int32_t(cid);
-                if (a.dt_next) my_dt = min(my_dt, (unsigned long long)__double_as_longlong(
-                                                    cfl_candidate<R>(Un, pr, cflR, dxR)));
             }
             __syncthreads();
-            // restriction of the fathers of the slab's octs (each oct's eight cells in order)
-            for (int w = tid; w < (FX / 2) * (FY / 2) * NV; w += nt) {
-                const int o = w / NV, v = w % NV, oi = o % (FX / 2), oj = o / (FX / 2);
-                const int q0 = 2 * oi + FX * (2 * oj);
-                const int32_t oct = sm.cell[q0] >> 3;
-                if (!tv.fused[oct]) continue;
-                double acc = 0.0;
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    acc += sm.U[v][q0 + (c & 1) + FX * ((c >> 1) & 1) + FX * FY * ((c >> 2) & 1)];
-                a.u_new[v * tv.ncell + tv.father[oct]] = 0.125 * acc;
-            }
+            if (!more) break;
+            predict(k + 3);
+            predict(k + 4);
+            __syncthreads();
+            slab_faces(k + 2);
             __syncthreads();
         }
+        // the last slab's restriction
+        for (int w = tid; w < NR; w += nt) restrict_one(z0 + a.zc - 2, w);
+        __syncthreads();
     }
     if (a.dt_next) {
         for (int off = 16; off > 0; off >>= 1) my_dt = min(my_dt, __shfl_xor_sync(0xffffffffu, my_dt, off));

@@ -124,10 +124,21 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         if (per[axis]) return (c + n) % n;
         return c < 0 ? 0 : n - 1;                  // outflow: clamp at this level
     };
-    auto cell_id = [&](int64_t X, int64_t Y, int64_t Z) -> int64_t {
-        const int64_t o = a.grid[(X >> 1) + M * ((Y >> 1) + M * (Z >> 1))];
-        return o * 8 + (X & 1) + 2 * (Y & 1) + 4 * (Z & 1);
+    // oct and cell ids fit in 32 bits (fewer than 2^27 octs); per-variable base pointers
+    // keep the 64-bit arithmetic out of the inner loops
+    const int32_t Mi = int32_t(M);
+    auto cell_id = [&](int64_t X, int64_t Y, int64_t Z) -> int32_t {
+        const int32_t x = int32_t(X), y = int32_t(Y), z = int32_t(Z);
+        const int32_t o = a.grid[(x >> 1) + Mi * ((y >> 1) + Mi * (z >> 1))];
+        return o * 8 + (x & 1) + 2 * (y & 1) + 4 * (z & 1);
     };
+    const double *uo[NV];
+    double *un[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        uo[v] = a.u_old + v * tv.ncell;
+        un[v] = a.u_new + v * tv.ncell;
+    }
 
     for (int64_t b = blockIdx.x; b < nfx * nfy * nseg; b += gridDim.x) {
         const int64_t fxy = b % (nfx * nfy), seg = b / (nfx * nfy);
@@ -140,10 +151,10 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 const int o = q >> 3, c = q & 7;
                 const int i = 2 * (o % (SX / 2)) + (c & 1), j = 2 * (o / (SX / 2)) + ((c >> 1) & 1);
                 const int64_t zp = 2 * L + ((c >> 2) & 1);
-                const int64_t cid = cell_id(wrap(X0 + i, 0), wrap(Y0 + j, 1), wrap(zp, 2));
+                const int32_t cid = cell_id(wrap(X0 + i, 0), wrap(Y0 + j, 1), wrap(zp, 2));
                 R Uw[NV], Wc[NV];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(a.u_old[v * tv.ncell + cid]);
+                for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(uo[v][cid]);
                 cons_to_prim_w(Uw, pr, Wc);
                 const int slot = int(zp & 3);
 #pragma unroll
@@ -234,17 +245,17 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 dU[v] = dU[v] + sm.Fz[q3(p)][v][r];
                 dU[v] = dU[v] - sm.Fz[q3(p + 1)][v][r];
             }
-            const int64_t cid = cell_id(X0 + 2 + x, Y0 + 2 + y, p);
+            const int32_t cid = cell_id(X0 + 2 + x, Y0 + 2 + y, p);
             const int ub = int((k >> 1) & 1);
             double Un[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                if (sizeof(R) == 8) Un[v] = a.u_old[v * tv.ncell + cid] + lam * to_state(dU[v]);
-                else Un[v] = a.u_old[v * tv.ncell + cid] + to_state(lamR * dU[v]);
-                a.u_new[v * tv.ncell + cid] = Un[v];
+                if (sizeof(R) == 8) Un[v] = uo[v][cid] + lam * to_state(dU[v]);
+                else Un[v] = uo[v][cid] + to_state(lamR * dU[v]);
+                un[v][cid] = Un[v];
                 sm.U[ub][v][q] = Un[v];
             }
-            sm.cell[ub][q] = int32_t(cid);
+            sm.cell[ub][q] = cid;
             if (a.dt_next) my_dt = min(my_dt, (unsigned long long)__double_as_longlong(cfl_candidate<R>(Un, pr, cflR, dxR)));
         };
         // restriction of the father of one oct of slab k (its eight cells in order), variable v
@@ -257,7 +268,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             double acc = 0.0;
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc += sm.U[ub][v][q0 + (c & 1) + FX * ((c >> 1) & 1) + FX * FY * ((c >> 2) & 1)];
-            a.u_new[v * tv.ncell + tv.father[oct]] = 0.125 * acc;
+            a.u_new[v * tv.ncell + tv.father[oct]] = 0.125 * acc;    // v is not a constant here
         };
 
         // prologue, keeping to the ring sizes (W: 4 planes, Q and Fz: 3): planes z0-2 .. z0+1,
@@ -290,10 +301,10 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                     const int q = w - NU, o = q >> 3, c = q & 7;
                     const int i = 2 * (o % (SX / 2)) + (c & 1), j = 2 * (o / (SX / 2)) + ((c >> 1) & 1);
                     const int64_t zp = k + 4 + ((c >> 2) & 1);
-                    const int64_t cid = cell_id(wrap(X0 + i, 0), wrap(Y0 + j, 1), wrap(zp, 2));
+                    const int32_t cid = cell_id(wrap(X0 + i, 0), wrap(Y0 + j, 1), wrap(zp, 2));
                     R Uw[NV], Wc[NV];
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(a.u_old[v * tv.ncell + cid]);
+                    for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(uo[v][cid]);
                     cons_to_prim_w(Uw, pr, Wc);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) sm.W[int(zp & 3)][v][i + SX * j] = Wc[v];

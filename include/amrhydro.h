@@ -122,6 +122,11 @@ typedef struct {
        that level (M = 2^(grid_level-1)), used by the z-column kernel; grid_level = 0 if none */
     int32_t grid_level;
     int32_t *grid;
+    /* batch mode, when every box is a multiple of 16 cells: the z-column kernel's work items
+       (8x8-cell footprints x 16-cell segments), box i owning [inst_col_off[i], inst_col_off[i+1]);
+       col_work = 0 if not available */
+    int64_t col_work;
+    int64_t *inst_col_off;
 } amr_tree;
 
 /* Sizes of the caller buffers amr_build_octree needs for this oct list (host list of

@@ -31,6 +31,10 @@ template <typename R, int FX, int FY> struct ColSmem {
 struct ColArgs {
     TreeView tv;
     const int32_t *grid;
+    // batch mode (n_inst > 0): per-box work offsets, octs lexicographic per box
+    int32_t n_inst;
+    const int64_t *inst_col_off, *inst_oct_off;
+    int64_t work;
     int level;
     int64_t n;              // cells per dimension
     int zc;                 // segment length in cells (multiple of 2, divides n)
@@ -108,30 +112,10 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
     Prm<R> pr;
     pr.gamma = to_work<R>(a.gamma); pr.rho_floor = to_work<R>(a.rho_floor); pr.p_floor = to_work<R>(a.p_floor);
     const R cflR = to_work<R>(a.cfl);
-    const int l = a.level;
-    const int64_t n = a.n, M = n / 2;
-    const double dx = pow2(-l);
-    const double lam = scale_pow2(*a.dt, l);     // dt / dx, exact
-    const R lamR = to_work<R>(lam);
-    const R hl = R(0.5) * lamR;
-    const R dxR = to_work<R>(dx);
+    const bool batch = a.n_inst > 0;
     const bool per[3] = {tv.bc[0] == AMR_BC_PERIODIC, tv.bc[2] == AMR_BC_PERIODIC, tv.bc[4] == AMR_BC_PERIODIC};
-    const int64_t nfx = n / FX, nfy = n / FY, nseg = n / a.zc;
     unsigned long long my_dt = ~0ull;
 
-    auto wrap = [&](int64_t c, int axis) -> int64_t {
-        if (c >= 0 && c < n) return c;
-        if (per[axis]) return (c + n) % n;
-        return c < 0 ? 0 : n - 1;                  // outflow: clamp at this level
-    };
-    // oct and cell ids fit in 32 bits (fewer than 2^27 octs); per-variable base pointers
-    // keep the 64-bit arithmetic out of the inner loops
-    const int32_t Mi = int32_t(M);
-    auto cell_id = [&](int64_t X, int64_t Y, int64_t Z) -> int32_t {
-        const int32_t x = int32_t(X), y = int32_t(Y), z = int32_t(Z);
-        const int32_t o = a.grid[(x >> 1) + Mi * ((y >> 1) + Mi * (z >> 1))];
-        return o * 8 + (x & 1) + 2 * (y & 1) + 4 * (z & 1);
-    };
     const double *uo[NV];
     double *un[NV];
 #pragma unroll
@@ -140,10 +124,50 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         un[v] = a.u_new + v * tv.ncell;
     }
 
-    for (int64_t b = blockIdx.x; b < nfx * nfy * nseg; b += gridDim.x) {
-        const int64_t fxy = b % (nfx * nfy), seg = b / (nfx * nfy);
+    for (int64_t b = blockIdx.x; b < a.work; b += gridDim.x) {
+        // geometry of this work item: the level (or the box), its column footprint and segment
+        int l = a.level;
+        int64_t n = a.n, wb = b;
+        int32_t obase = 0;                        // batch: first oct of the box
+        double dx, lam;
+        double *dtn = a.dt_next;
+        if (batch) {
+            int lo = 0, hi = a.n_inst - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.inst_col_off[mid] <= b) lo = mid; else hi = mid - 1;
+            }
+            n = tv.inst_n[lo];
+            wb = b - a.inst_col_off[lo];
+            obase = int32_t(a.inst_oct_off[lo]);
+            dx = tv.inst_dx[lo];
+            lam = a.dt[lo] * double(n);
+            dtn = a.dt_next ? a.dt_next + lo : nullptr;
+        } else {
+            dx = pow2(-l);
+            lam = scale_pow2(*a.dt, l);           // dt / dx, exact
+        }
+        const int64_t M = n / 2;
+        const R lamR = to_work<R>(lam);
+        const R hl = R(0.5) * lamR;
+        const R dxR = to_work<R>(dx);
+        const int64_t nfx = n / FX, nfy = n / FY;
+        const int64_t fxy = wb % (nfx * nfy), seg = wb / (nfx * nfy);
         const int64_t X0 = (fxy % nfx) * FX - 2, Y0 = (fxy / nfx) * FY - 2;   // stencil index 0
         const int64_t z0 = seg * a.zc;
+        auto wrap = [&](int64_t c, int axis) -> int64_t {
+            if (c >= 0 && c < n) return c;
+            if (per[axis]) return (c + n) % n;
+            return c < 0 ? 0 : n - 1;              // outflow: clamp at this level
+        };
+        // oct and cell ids fit in 32 bits (fewer than 2^27 octs)
+        const int32_t Mi = int32_t(M);
+        auto cell_id = [&](int64_t X, int64_t Y, int64_t Z) -> int32_t {
+            const int32_t x = int32_t(X), y = int32_t(Y), z = int32_t(Z);
+            const int32_t oi = (x >> 1) + Mi * ((y >> 1) + Mi * (z >> 1));
+            const int32_t o = batch ? obase + oi : a.grid[oi];
+            return o * 8 + (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+        };
 
         // gather oct layer L (cell planes 2L, 2L+1) of the stencil footprint into the W ring
         auto gather = [&](int64_t L) {
@@ -256,7 +280,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 sm.U[ub][v][q] = Un[v];
             }
             sm.cell[ub][q] = cid;
-            if (a.dt_next) my_dt = min(my_dt, (unsigned long long)__double_as_longlong(cfl_candidate<R>(Un, pr, cflR, dxR)));
+            if (dtn) my_dt = min(my_dt, (unsigned long long)__double_as_longlong(cfl_candidate<R>(Un, pr, cflR, dxR)));
         };
         // restriction of the father of one oct of slab k (its eight cells in order), variable v
         auto restrict_one = [&](int64_t k, int w) {
@@ -309,7 +333,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
 #pragma unroll
                     for (int v = 0; v < NV; ++v) sm.W[int(zp & 3)][v][i + SX * j] = Wc[v];
                 } else {
-                    restrict_one(k - 2, w - NU - (more ? NG : 0));
+                    if (!batch) restrict_one(k - 2, w - NU - (more ? NG : 0));
                 }
             }
             __syncthreads();
@@ -321,7 +345,14 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             __syncthreads();
         }
         // the last slab's restriction
-        for (int w = tid; w < NR; w += nt) restrict_one(z0 + a.zc - 2, w);
+        if (!batch)
+            for (int w = tid; w < NR; w += nt) restrict_one(z0 + a.zc - 2, w);
+        if (batch && dtn) {
+            // boxes have their own time steps: reduce this work item's candidates now
+            for (int off = 16; off > 0; off >>= 1) my_dt = min(my_dt, __shfl_xor_sync(0xffffffffu, my_dt, off));
+            if ((tid & 31) == 0 && my_dt != ~0ull) atomicMin(reinterpret_cast<unsigned long long *>(dtn), my_dt);
+            my_dt = ~0ull;
+        }
         __syncthreads();
     }
     if (a.dt_next) {
@@ -338,17 +369,27 @@ amr_status launch_col(const amr_tree *t, const hydro_params *p, const double *u_
     ColArgs a;
     a.tv = make_view(t);
     a.grid = t->grid;
-    a.level = t->grid_level;
-    a.n = int64_t(1) << t->grid_level;
-    a.zc = a.n < 32 ? int(a.n) : 32;
+    a.n_inst = t->n_inst;
+    a.inst_col_off = t->inst_col_off;
+    a.inst_oct_off = t->inst_oct_off;
+    if (t->n_inst > 0) {
+        a.level = 0;
+        a.n = 0;
+        a.zc = 16;
+        a.work = t->col_work;
+    } else {
+        a.level = t->grid_level;
+        a.n = int64_t(1) << t->grid_level;
+        a.zc = a.n < 32 ? int(a.n) : 32;
+        a.work = (a.n / FX) * (a.n / FY) * (a.n / a.zc);
+    }
     a.u_old = u_old; a.u_new = u_new; a.dt = dt; a.dt_next = dt_next;
     a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
     a.status = p->d_status;
     const size_t bytes = sizeof(ColSmem<R, FX, FY>);
     auto kern = k_godunov_col<R, RS, FX, FY>;
     AMR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
-    const int64_t work = (a.n / FX) * (a.n / FY) * (a.n / a.zc);
-    kern<<<unsigned(work < 1048576 ? work : 1048576), 256, bytes, st>>>(a);
+    kern<<<unsigned(a.work < 1048576 ? a.work : 1048576), 256, bytes, st>>>(a);
     AMR_CUDA_TRY(cudaGetLastError());
     return AMR_OK;
 }

@@ -584,8 +584,13 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
     if (depth != 1 && depth != 2) return AMR_EINVAL;
     if (depth == 2 && sizeof(R) == 8) return AMR_EINVAL;   // an FP64 12^3-cell stencil does not fit in smem
     if (t->n_inst > 0) {
-        // batch mode: every tile of every box in one launch
+        // batch mode: every box in one launch (z-column kernel when every box is a multiple of
+        // 16 cells, else tiles)
         if (level != -1) return AMR_EINVAL;
+        if (!p->tiles_only && p->riemann != AMR_RIEMANN_MLP && t->col_work > 0)
+            return p->riemann == AMR_RIEMANN_EXACT
+                       ? launch_col<R, AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, st)
+                       : launch_col<R, AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, st);
         if (depth == 2 && t->tile_off[1][1] == 0) depth = 1;            // some box is not a multiple of 8
         if (p->riemann == AMR_RIEMANN_MLP) depth = 1;
         const int d = depth;

@@ -296,7 +296,7 @@ __global__ void k_tile_slots(BuildView b, int depth, int64_t ntile, const int32_
 
 // ---- batch mode: independent uniform boxes -------------------------------------------
 struct BoxLayout {
-    size_t lvl, ix, iy, iz, refmask, fused, inst_n, inst_dx, inst_oct_off, root[2], slot[2], tinst[2], total;
+    size_t lvl, ix, iy, iz, refmask, fused, inst_n, inst_dx, inst_oct_off, col_off, root[2], slot[2], tinst[2], total;
     int64_t noct, ntile[2];
 };
 
@@ -329,6 +329,7 @@ static BoxLayout box_layout(const amr_geom *g, int64_t n, const int64_t nt[2])
     L.refmask = put(n); L.fused = put(n);
     L.inst_n = put(4 * size_t(g->n_inst)); L.inst_dx = put(8 * size_t(g->n_inst));
     L.inst_oct_off = put(8 * (size_t(g->n_inst) + 1));
+    L.col_off = put(8 * (size_t(g->n_inst) + 1));
     for (int d = 0; d < 2; ++d) {
         L.root[d] = put(4 * nt[d]);
         L.slot[d] = put(4 * nt[d] * nslot(d + 1));
@@ -406,8 +407,10 @@ static amr_status build_boxes(const amr_geom *g, void *d_tree_mem, size_t tree_b
     out->inst_n = (int32_t *)(T + L.inst_n);
     out->inst_dx = (double *)(T + L.inst_dx);
     out->inst_oct_off = (int64_t *)(T + L.inst_oct_off);
-    std::vector<int64_t> ooff(g->n_inst + 1), toff[2];
+    std::vector<int64_t> ooff(g->n_inst + 1), toff[2], coff(g->n_inst + 1);
     std::vector<double> dx(g->n_inst);
+    bool col_ok = true;
+    coff[0] = 0;
     toff[0].resize(g->n_inst + 1); toff[1].resize(g->n_inst + 1);
     ooff[0] = toff[0][0] = toff[1][0] = 0;
     for (int i = 0; i < g->n_inst; ++i) {
@@ -416,7 +419,12 @@ static amr_status build_boxes(const amr_geom *g, void *d_tree_mem, size_t tree_b
         toff[0][i + 1] = toff[0][i] + (N / 4) * (N / 4) * (N / 4);
         toff[1][i + 1] = toff[1][i] + (nt[1] ? (N / 8) * (N / 8) * (N / 8) : 0);
         dx[i] = 1.0 / double(N);
+        if (N % 16) col_ok = false;
+        coff[i + 1] = coff[i] + (N / 8) * (N / 8) * (N / 16);   // 8x8 footprints x 16-cell segments
     }
+    out->inst_col_off = (int64_t *)(T + L.col_off);
+    out->col_work = col_ok ? coff[g->n_inst] : 0;
+    AMR_CUDA_TRY(cudaMemcpyAsync(out->inst_col_off, coff.data(), 8 * coff.size(), cudaMemcpyHostToDevice, st));
     int64_t *t0 = (int64_t *)S, *t1 = (int64_t *)(S + al256(8 * (size_t(g->n_inst) + 1)));
     int32_t *dbc = (int32_t *)(S + 2 * al256(8 * (size_t(g->n_inst) + 1)));
     AMR_CUDA_TRY(cudaMemcpyAsync(out->inst_n, g->h_inst_n, 4 * size_t(g->n_inst), cudaMemcpyHostToDevice, st));

@@ -102,3 +102,37 @@ def test_batch_rejects_bad_sizes(H):
     from paper_2411_14631_gb300 import abi
     with pytest.raises(abi.AmrError):
         H.Octree.boxes(np.array([16, 18], dtype=np.int32))
+
+
+@pytest.mark.parametrize("bc", [(1,) * 6, (0,) * 6])
+def test_batch_column_kernel(oracle, H, bc):
+    """Boxes that are all multiples of 16 cells run on the z-column kernel: FP64 against
+    the box oracle, and bitwise equal to the tile kernel (tiles_only) in FP64 and FP32."""
+    import torch
+    sizes = np.array([16, 32, 48, 16], dtype=np.int32)
+    tree = H.Octree.boxes(sizes, bc)
+    assert tree.t.col_work > 0
+    fields = {int(N): _box_fields(int(N), 50 + k) for k, N in enumerate(sizes)}
+    w0 = W.batch_prims(sizes, lambda N: fields[N])
+    res = {}
+    for precision in (0, 1):
+        for tiles_only in (False, True):
+            sim = H.Simulation(tree, H.Params(1.4, cfl=0.6, precision=precision, tiles_only=tiles_only), w0=w0)
+            for _ in range(3):
+                sim.step()
+            torch.cuda.synchronize()
+            res[(precision, tiles_only)] = (sim.u.cpu().numpy(), sim.dt.cpu().numpy())
+    for precision in (0, 1):
+        assert np.array_equal(res[(precision, False)][0], res[(precision, True)][0])
+        assert np.array_equal(res[(precision, False)][1], res[(precision, True)][1])
+    prm_o = oracle.params(gamma=1.4, cfl=0.6)
+    ug = res[(0, False)][0]
+    for b, N in enumerate(sizes):
+        N = int(N)
+        U = _cons_lex(oracle, fields[N], 1.4)
+        for _ in range(3):
+            U, st = oracle.box_step(N, bc, U, prm_o, oracle.box_courant(N, U, prm_o))
+        seg = ug[:, tree.cell_off[b]:tree.cell_off[b + 1]]
+        ref = U[:, W.box_batch_to_lex(N)]
+        for v in range(5):
+            assert np.max(np.abs(seg[v] - ref[v])) <= 1e-12 * np.max(np.abs(ref[v])), (b, v)

@@ -73,8 +73,8 @@ typedef struct {
    riemann: AMR_RIEMANN_*; precision: AMR_PREC_FP64 (all arithmetic in FP64) or
    AMR_PREC_FP32 (reconstruction and Riemann solve in FP32, state accumulation in FP64);
    tile: 1 or 2 = depth of the oct tiles a CTA updates (8 or 64 octs), 0 = default;
-   tiles_only: 0 = a complete finest level (uniform, nothing refined) is updated by the
-   z-column kernel (same arithmetic per cell, less ghost work), 1 = tiles for every level;
+   tiles_only: 0 = the deepest complete level is updated by the z-column kernel (the
+   same arithmetic per cell as the tiles, less ghost work), 1 = tiles for every level;
    mlp_weights: device pointer to the surrogate's weights (AMR_RIEMANN_MLP only);
    mlp_resid_tol: acceptance threshold of the surrogate's residual check;
    d_status: device int32 error word (may be NULL); d_counters: device uint64
@@ -118,8 +118,8 @@ typedef struct {
     double *inst_dx;                        /* device [n_inst]: 1 / N */
     int64_t *inst_oct_off;                  /* device [n_inst + 1] */
     int32_t *tile_inst[2];                  /* device, per tile: box index (batch mode) */
-    /* octree mode, when the finest level is complete: grid[ix + M (iy + M iz)] = oct index of
-       that level (M = 2^(grid_level-1)), used by the z-column kernel; grid_level = 0 if none */
+    /* octree mode: grid[ix + M (iy + M iz)] = oct index of the deepest complete level
+       grid_level (levelmin at least; M = 2^(grid_level-1)), used by the z-column kernel */
     int32_t grid_level;
     int32_t *grid;
     /* batch mode, when every box is a multiple of 16 cells: the z-column kernel's work items

@@ -26,6 +26,8 @@ template <typename R, int FX, int FY> struct ColSmem {
     R Fz[3][NV][FY * FX];                            // face below plane j, slot (j + 6) % 3
     double U[2][NV][2 * FY * FX];                    // new states of the last two slabs
     int32_t cell[2][2 * FY * FX];                    // their cell ids (oct*8 + c)
+    uint8_t ref[8][SY * SX];                         // refined flag of each stencil cell, slot = plane & 7
+                                                     // (live: k-1 .. k+5, longer than the W ring)
 };
 
 struct ColArgs {
@@ -35,6 +37,7 @@ struct ColArgs {
     int32_t n_inst;
     const int64_t *inst_col_off, *inst_oct_off;
     int64_t work;
+    int32_t finer;          // the level has refined cells (finer levels exist)
     int level;
     int64_t n;              // cells per dimension
     int zc;                 // segment length in cells (multiple of 2, divides n)
@@ -183,6 +186,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 const int slot = int(zp & 3);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) sm.W[slot][v][i + SX * j] = Wc[v];
+                if (a.finer) sm.ref[int(zp & 7)][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
             }
         };
         auto q3 = [](int64_t p) { return int((p + 6) % 3); };   // planes start at z0 - 2 >= -2
@@ -259,18 +263,29 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         auto update = [&](int64_t k, int q) {
             const int dz = q / (FX * FY), r = q % (FX * FY), x = r % FX, y = r / FX;
             const int64_t p = k + dz;
+            const int ub = int((k >> 1) & 1);
+            // with finer levels: a refined cell is left to the restriction, and a face whose
+            // other side is refined carries no flux here (the finer level supplies it)
+            bool sk[6] = {false, false, false, false, false, false};
+            if (a.finer) {
+                const int si = (x + 2) + SX * (y + 2);
+                const uint8_t *rp = sm.ref[int(p & 7)];
+                if (rp[si]) { sm.cell[ub][q] = -1; return; }
+                sk[0] = rp[si - 1]; sk[1] = rp[si + 1]; sk[2] = rp[si - SX]; sk[3] = rp[si + SX];
+                sk[4] = sm.ref[int((p - 1) & 7)][si]; sk[5] = sm.ref[int((p + 1) & 7)][si];
+            }
             R dU[NV] = {0, 0, 0, 0, 0};
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                dU[v] = dU[v] + sm.Fx[dz][v][x + (FX + 1) * y];
-                dU[v] = dU[v] - sm.Fx[dz][v][x + 1 + (FX + 1) * y];
-                dU[v] = dU[v] + sm.Fy[dz][v][x + FX * y];
-                dU[v] = dU[v] - sm.Fy[dz][v][x + FX * (y + 1)];
-                dU[v] = dU[v] + sm.Fz[q3(p)][v][r];
-                dU[v] = dU[v] - sm.Fz[q3(p + 1)][v][r];
+                if (!sk[0]) dU[v] = dU[v] + sm.Fx[dz][v][x + (FX + 1) * y];
+                if (!sk[1]) dU[v] = dU[v] - sm.Fx[dz][v][x + 1 + (FX + 1) * y];
+                if (!sk[2]) dU[v] = dU[v] + sm.Fy[dz][v][x + FX * y];
+                if (!sk[3]) dU[v] = dU[v] - sm.Fy[dz][v][x + FX * (y + 1)];
+                if (!sk[4]) dU[v] = dU[v] + sm.Fz[q3(p)][v][r];
+                if (!sk[5]) dU[v] = dU[v] - sm.Fz[q3(p + 1)][v][r];
             }
+            const bool nbref = sk[0] || sk[1] || sk[2] || sk[3] || sk[4] || sk[5];
             const int32_t cid = cell_id(X0 + 2 + x, Y0 + 2 + y, p);
-            const int ub = int((k >> 1) & 1);
             double Un[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -280,14 +295,16 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 sm.U[ub][v][q] = Un[v];
             }
             sm.cell[ub][q] = cid;
-            if (dtn) my_dt = min(my_dt, (unsigned long long)__double_as_longlong(cfl_candidate<R>(Un, pr, cflR, dxR)));
+            if (dtn && !nbref) my_dt = min(my_dt, (unsigned long long)__double_as_longlong(cfl_candidate<R>(Un, pr, cflR, dxR)));
         };
         // restriction of the father of one oct of slab k (its eight cells in order), variable v
         auto restrict_one = [&](int64_t k, int w) {
             const int o = w / NV, v = w % NV, oi = o % (FX / 2), oj = o / (FX / 2);
             const int ub = int((k >> 1) & 1);
             const int q0 = 2 * oi + FX * (2 * oj);
-            const int32_t oct = sm.cell[ub][q0] >> 3;
+            const int32_t c0 = sm.cell[ub][q0];
+            if (c0 < 0) return;                       // a refined cell: the oct is not restricted here
+            const int32_t oct = c0 >> 3;
             if (!tv.fused[oct]) return;
             double acc = 0.0;
 #pragma unroll
@@ -332,6 +349,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                     cons_to_prim_w(Uw, pr, Wc);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) sm.W[int(zp & 3)][v][i + SX * j] = Wc[v];
+                    if (a.finer) sm.ref[int(zp & 7)][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
                 } else {
                     if (!batch) restrict_one(k - 2, w - NU - (more ? NG : 0));
                 }
@@ -372,6 +390,7 @@ amr_status launch_col(const amr_tree *t, const hydro_params *p, const double *u_
     a.n_inst = t->n_inst;
     a.inst_col_off = t->inst_col_off;
     a.inst_oct_off = t->inst_oct_off;
+    a.finer = t->n_inst == 0 && t->grid_level < t->levelmax;
     if (t->n_inst > 0) {
         a.level = 0;
         a.n = 0;

@@ -618,17 +618,24 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
             return d == 1 ? launch<R, 1, AMR_RIEMANN_EXACT>(a, nt, st) : launch<R, D2, AMR_RIEMANN_EXACT>(a, nt, st);
         return d == 1 ? launch<R, 1, AMR_RIEMANN_HLLC>(a, nt, st) : launch<R, D2, AMR_RIEMANN_HLLC>(a, nt, st);
     }
+    // level: >= 0 one level, -1 all levels, <= -2 the range encoded as -2 - (hi << 8 | lo)
     int l0 = level < 0 ? t->levelmin : level, l1 = level < 0 ? t->levelmax : level;
+    if (level <= -2) { l0 = (-2 - level) & 255; l1 = (-2 - level) >> 8; }
     if (l0 < t->levelmin || l1 > t->levelmax) return AMR_EINVAL;
-    // a complete finest level goes to the z-column kernel (bitwise the same per cell)
-    if (!p->tiles_only && p->riemann != AMR_RIEMANN_MLP && t->grid && t->grid_level == t->levelmax &&
-        t->grid_level >= 3 && l1 == t->grid_level) {
+    // the deepest complete level goes to the z-column kernel (bitwise the same per cell);
+    // the levels below and above it to the tile kernel
+    const int gl = t->grid_level;
+    if (!p->tiles_only && p->riemann != AMR_RIEMANN_MLP && t->grid && gl >= 3 && gl >= l0 && gl <= l1) {
         const amr_status r = p->riemann == AMR_RIEMANN_EXACT
                                  ? launch_col<R, AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, st)
                                  : launch_col<R, AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, st);
         if (r != AMR_OK) return r;
-        l1 = t->grid_level - 1;
-        if (l0 > l1) return AMR_OK;
+        // levels below a complete level have no leaf cells: nothing of theirs survives the
+        // restriction, so they are not updated
+        hydro_params q = *p;
+        q.tiles_only = 1;
+        if (gl < l1) return dispatch_impl<R>(t, -2 - (l1 << 8 | (gl + 1)), &q, u_old, u_new, reg, dt, dt_next, st);
+        return AMR_OK;
     }
     int lsplit = l0;
     while (lsplit <= l1 && lsplit - depth < 1) ++lsplit;

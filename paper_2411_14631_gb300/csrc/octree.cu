@@ -37,8 +37,10 @@ static TreeLayout tree_layout(int64_t n, const int64_t cnt[AMR_MAXLEV + 2], int 
     L.lvl = put(4 * n); L.ix = put(4 * n); L.iy = put(4 * n); L.iz = put(4 * n);
     L.key = put(8 * n); L.son = put(32 * n); L.father = put(4 * n); L.nbor = put(24 * n);
     L.nb27 = put(108 * n); L.refmask = put(n); L.fused = put(n);
-    // dense oct grid of the finest level when it is complete
-    L.grid = put(cnt[lmax] == (int64_t(1) << (3 * (lmax - 1))) ? 4 * cnt[lmax] : 0);
+    // dense oct grid of the deepest complete level
+    int lg = lmax;
+    while (lg > levelmin && cnt[lg] != (int64_t(1) << (3 * (lg - 1)))) --lg;
+    L.grid = put(4 * cnt[lg]);
     for (int d = 0; d < 2; ++d) {
         L.root[d] = put(4 * L.tile_bound[d]);
         L.slot[d] = put(4 * L.tile_bound[d] * nslot(d + 1));
@@ -552,11 +554,14 @@ extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oc
     bv.lvl = out->lvl; bv.ix = out->ix; bv.iy = out->iy; bv.iz = out->iz; bv.key = out->key;
     k_tables<<<nb, TB, 0, st>>>(bv, out->son, out->father, out->nbor, out->nb27, out->refmask, err);
     k_fused<<<nb, TB, 0, st>>>(bv, out->son, out->nbor, out->refmask, out->fused);
-    if (cnt[lmax] == (int64_t(1) << (3 * (lmax - 1))) && lmax >= lmin) {
-        out->grid_level = lmax;
+    {
+        // the deepest complete level (levelmin at least): its oct grid for the z-column kernel
+        int lg = lmax;
+        while (lg > lmin && cnt[lg] != (int64_t(1) << (3 * (lg - 1)))) --lg;
+        out->grid_level = lg;
         out->grid = (int32_t *)(T + L.grid);
-        const int64_t nl = cnt[lmax];
-        k_grid<<<unsigned((nl + TB - 1) / TB), TB, 0, st>>>(out->lvl_off[lmax], out->lvl_off[lmax + 1], lmax, out->ix,
+        const int64_t nl = cnt[lg];
+        k_grid<<<unsigned((nl + TB - 1) / TB), TB, 0, st>>>(out->lvl_off[lg], out->lvl_off[lg + 1], lg, out->ix,
                                                             out->iy, out->iz, out->grid);
     }
 

@@ -281,3 +281,27 @@ def test_column_kernel_equals_tiles(oracle, H, level, precision, riemann, bc):
         res.append((sim.u.cpu().numpy(), sim.dt.cpu().numpy()))
     assert np.array_equal(res[0][0], res[1][0])
     assert np.array_equal(res[0][1], res[1][1])
+
+
+@pytest.mark.parametrize("seed,periodic,precision", [(70, True, 0), (71, False, 1), (72, True, 1)])
+def test_column_kernel_with_refinement_equals_tiles(oracle, H, seed, periodic, precision):
+    """The deepest complete level of an AMR tree runs on the z-column kernel (faces next to
+    refined cells skipped, refined cells left to the restriction); it matches the tile
+    kernel bit for bit, states and time steps."""
+    import torch
+    lx = W.random_tree(4, 2, seed, p_refine=0.3, periodic=periodic)
+    bc = PER if periodic else OUT
+    g = H.Octree(lx, 4, bc)
+    assert g.t.grid_level == 4 and g.levelmax >= 5
+    t = oracle.Tree(lx, 4, bc)
+    xyz, _ = t.cell_centres()
+    w0 = _smooth_random(xyz, seed)
+    res = []
+    for tiles_only in (False, True):
+        sim = H.Simulation(g, H.Params(5 / 3, cfl=0.6, precision=precision, tiles_only=tiles_only), w0=w0)
+        for _ in range(3):
+            sim.step()
+        torch.cuda.synchronize()
+        res.append((sim.u.cpu().numpy(), sim.dt.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])

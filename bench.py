@@ -175,23 +175,57 @@ def time_graph(H, tree, prm, w0, steps, warmup):
 
 
 def time_e2e(H, tree, prm, w0, steps, stream):
-    """Public-API end to end: per step, H2D of the state from pinned host memory,
-    hydro_step, D2H of the new state to pinned host memory."""
+    """Public-API end to end: every step copies its input state from pinned host memory to
+    the device, runs hydro_step, and copies the new state back to pinned host memory.
+    Steps are independent (each starts from the host input), so they are pipelined over
+    three streams with two device slots: the copy-in of step k+1 and the copy-out of step
+    k-1 overlap the update of step k (one copy engine each way)."""
     import torch
     sim = H.Simulation(tree, prm, w0=w0)
     host_in = torch.empty_like(sim.u, device="cpu").pin_memory()
     host_in.copy_(sim.u.cpu())
-    host_out = torch.empty_like(host_in).pin_memory()
+    host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
+    u_in = [sim.u, sim.u_new]
+    u_out = [torch.empty_like(sim.u) for _ in range(2)]
+    reg = sim.reg
+    dt = sim.dt
+    dtn = [torch.empty_like(sim.dt) for _ in range(2)]
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    e_in = [torch.cuda.Event() for _ in range(2)]
+    e_cmp = [torch.cuda.Event() for _ in range(2)]
+    e_out = [torch.cuda.Event() for _ in range(2)]
+    e_free_in = [torch.cuda.Event() for _ in range(2)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        torch.cuda.synchronize()
-        t0.record(stream)
-        for _ in range(steps):
-            sim.u.copy_(host_in, non_blocking=True)
-            H.hydro_step(tree, prm, sim.u, sim.u_new, sim.reg, sim.dt, sim.dt_next, stream)
-            host_out.copy_(sim.u_new, non_blocking=True)
-        t1.record(stream)
-        t1.synchronize()
+
+    def run(nsteps):
+        for k in range(nsteps):
+            j = k % 2
+            if k >= 2:
+                s_in.wait_event(e_free_in[j])            # step k-2 finished reading u_in[j]
+            with torch.cuda.stream(s_in):
+                u_in[j].copy_(host_in, non_blocking=True)
+                e_in[j].record(s_in)
+            s_cmp.wait_event(e_in[j])
+            if k >= 2:
+                s_cmp.wait_event(e_out[j])               # step k-2's copy-out of u_out[j] done
+            H.hydro_step(tree, prm, u_in[j], u_out[j], reg, dt, dtn[j], stream=s_cmp)
+            e_cmp[j].record(s_cmp)
+            e_free_in[j].record(s_cmp)
+            s_out.wait_event(e_cmp[j])
+            with torch.cuda.stream(s_out):
+                host_out[j].copy_(u_out[j], non_blocking=True)
+                e_out[j].record(s_out)
+
+    run(2)                                               # warm-up
+    torch.cuda.synchronize()
+    t0.record(s_in)
+    s_cmp.wait_event(t0)
+    s_out.wait_event(t0)
+    run(steps)
+    s_out.wait_stream(s_cmp)
+    s_out.wait_stream(s_in)
+    t1.record(s_out)
+    t1.synchronize()
     ms = t0.elapsed_time(t1) / steps
     nbytes = sim.u.numel() * 8
     return ms, nbytes

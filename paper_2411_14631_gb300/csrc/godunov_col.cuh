@@ -16,7 +16,7 @@
 
 namespace amr {
 
-template <typename R, int FX, int FY> struct ColSmem {
+template <typename R, int FX, int FY, bool FINER> struct ColSmem {
     static constexpr int SX = FX + 4, SY = FY + 4;   // stencil footprint (cells)
     static constexpr int PX = FX + 2, PY = FY + 2;   // predicted footprint
     R W[4][NV][SY * SX];                             // ring, slot = plane & 3 (live: k .. k+3)
@@ -26,8 +26,9 @@ template <typename R, int FX, int FY> struct ColSmem {
     R Fz[3][NV][FY * FX];                            // face below plane j, slot (j + 6) % 3
     double U[2][NV][2 * FY * FX];                    // new states of the last two slabs
     int32_t cell[2][2 * FY * FX];                    // their cell ids (oct*8 + c)
-    uint8_t ref[8][SY * SX];                         // refined flag of each stencil cell, slot = plane & 7
-                                                     // (live: k-1 .. k+5, longer than the W ring)
+    // refined flag of each stencil cell, slot = plane & 7 (live: k-1 .. k+5, longer than the
+    // W ring); only when the level has finer levels (keeps 4 CTAs per SM otherwise)
+    uint8_t ref[FINER ? 8 : 1][FINER ? SY * SX : 1];
 };
 
 struct ColArgs {
@@ -103,10 +104,10 @@ __device__ __forceinline__ void col_store(R (*F)[N], int r, const R Fn[NV])
     F[4][r] = Fn[4];
 }
 
-template <typename R, int RS, int FX, int FY>
+template <typename R, int RS, int FX, int FY, bool FINER>
 __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
 {
-    using S = ColSmem<R, FX, FY>;
+    using S = ColSmem<R, FX, FY, FINER>;
     constexpr int SX = S::SX, SY = S::SY, PX = S::PX, PY = S::PY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 const int slot = int(zp & 3);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) sm.W[slot][v][i + SX * j] = Wc[v];
-                if (a.finer) sm.ref[int(zp & 7)][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
+                if constexpr (FINER) sm.ref[int(zp & 7)][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
             }
         };
         auto q3 = [](int64_t p) { return int((p + 6) % 3); };   // planes start at z0 - 2 >= -2
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             // with finer levels: a refined cell is left to the restriction, and a face whose
             // other side is refined carries no flux here (the finer level supplies it)
             bool sk[6] = {false, false, false, false, false, false};
-            if (a.finer) {
+            if constexpr (FINER) {
                 const int si = (x + 2) + SX * (y + 2);
                 const uint8_t *rp = sm.ref[int(p & 7)];
                 if (rp[si]) { sm.cell[ub][q] = -1; return; }
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                     cons_to_prim_w(Uw, pr, Wc);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) sm.W[int(zp & 3)][v][i + SX * j] = Wc[v];
-                    if (a.finer) sm.ref[int(zp & 7)][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
+                    if constexpr (FINER) sm.ref[int(zp & 7)][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
                 } else {
                     if (!batch) restrict_one(k - 2, w - NU - (more ? NG : 0));
                 }
@@ -405,8 +406,9 @@ amr_status launch_col(const amr_tree *t, const hydro_params *p, const double *u_
     a.u_old = u_old; a.u_new = u_new; a.dt = dt; a.dt_next = dt_next;
     a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
     a.status = p->d_status;
-    const size_t bytes = sizeof(ColSmem<R, FX, FY>);
-    auto kern = k_godunov_col<R, RS, FX, FY>;
+    const bool finer = a.finer != 0;
+    const size_t bytes = finer ? sizeof(ColSmem<R, FX, FY, true>) : sizeof(ColSmem<R, FX, FY, false>);
+    auto kern = finer ? k_godunov_col<R, RS, FX, FY, true> : k_godunov_col<R, RS, FX, FY, false>;
     AMR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
     kern<<<unsigned(a.work < 1048576 ? a.work : 1048576), 256, bytes, st>>>(a);
     AMR_CUDA_TRY(cudaGetLastError());

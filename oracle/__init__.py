@@ -9,7 +9,7 @@ written in the source).
 The scheme it writes out (the paper prints none; Table 1 only names godunov_fine,
 newdt_fine and refine_fine) is documented at the top of ``hydro.c``; the Riemann
 solvers in ``riemann.c``; the octree and Hilbert key in ``tree.c``; the surrogate
-network in ``mlp.c``.
+network in ``mlp.c``; the CG and PPCG Poisson solvers of Sec. 2.3 in ``poisson.c``.
 """
 import ctypes as C
 import os
@@ -18,10 +18,11 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = ["riemann.c", "tree.c", "hydro.c", "mlp.c", "box.c"]
+_SRC = ["riemann.c", "tree.c", "hydro.c", "mlp.c", "box.c", "poisson.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
-OK, EINVAL, EUNBALANCED, ENONPHYSICAL, ENOCONV = 0, -1, -2, -6, -7
+OK, EINVAL, EUNBALANCED, ENONPHYSICAL, ENOCONV, EBREAKDOWN = 0, -1, -2, -6, -7, -8
+PRECOND_NONE, PRECOND_IP = 0, 1
 PERIODIC, OUTFLOW = 0, 1
 HLLC, EXACT = 0, 1
 OUTSIDE = -(2 ** 31)
@@ -86,6 +87,11 @@ def lib():
         L.or_mlp_backward.argtypes = [P, P, P, C.c_int64, P, P]
         L.or_adam_step.argtypes = [P, P, P, P, C.c_int64, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_int64]
+        I = C.c_int
+        L.or_poisson_apply_A.argtypes = [I, I, I, P, P]
+        L.or_poisson_apply_Minv.argtypes = [I, I, I, I, P, P]
+        for f in (L.or_cg, L.or_ppcg):
+            f.argtypes = [I, I, I, I, P, P, C.c_double, I, P, C.POINTER(C.c_int)]
         _lib = L
     return _lib
 
@@ -303,3 +309,43 @@ def adam_step(theta, m, v, grad, lr, beta1, beta2, eps, t):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     grad = _f64(grad)
     lib().or_adam_step(_p(theta), _p(m), _p(v), _p(grad), theta.size, lr, beta1, beta2, eps, t)
+
+
+# ---- Poisson solve (Sec. 2.3) ---------------------------------------------------
+def poisson_apply_A(shape, x):
+    """y = A x, A = 6 I - (sum over in-box face neighbours); shape = (nx, ny, nz),
+    vectors indexed i + nx (j + ny k)."""
+    nx, ny, nz = shape
+    x = _f64(x).ravel()
+    y = np.empty_like(x)
+    lib().or_poisson_apply_A(nx, ny, nz, _p(x), _p(y))
+    return y
+
+
+def poisson_apply_Minv(shape, r, precond=PRECOND_IP):
+    nx, ny, nz = shape
+    r = _f64(r).ravel()
+    u = np.empty_like(r)
+    lib().or_poisson_apply_Minv(nx, ny, nz, precond, _p(r), _p(u))
+    return u
+
+
+def _krylov(fn, shape, b, x0, precond, tol, maxit):
+    nx, ny, nz = shape
+    b = _f64(b).ravel()
+    x = np.zeros_like(b) if x0 is None else _f64(x0).ravel().copy()
+    eps = np.full(maxit + 1, np.nan)
+    it = C.c_int()
+    st = fn(nx, ny, nz, precond, _p(b), _p(x), tol, maxit, _p(eps), C.byref(it))
+    return x, eps[:it.value + 1].copy(), it.value, st
+
+
+def cg(shape, b, x0=None, precond=PRECOND_NONE, tol=1e-4, maxit=1000):
+    """Textbook (preconditioned) CG; returns (x, eps history per Eq. 3, iterations, status)."""
+    return _krylov(lib().or_cg, shape, b, x0, precond, tol, maxit)
+
+
+def ppcg(shape, b, x0=None, precond=PRECOND_IP, tol=1e-4, maxit=1000):
+    """Preconditioned pipelined CG (Ghysels & Vanroose 2014, Algorithm 4) as adopted in
+    Sec. 2.3; returns (x, eps history per Eq. 3, iterations, status)."""
+    return _krylov(lib().or_ppcg, shape, b, x0, precond, tol, maxit)

@@ -25,7 +25,8 @@
 #define OR_MAXLEV 21
 #define OR_NVAR 5
 
-enum { OR_OK = 0, OR_EINVAL = -1, OR_EUNBALANCED = -2, OR_ENONPHYSICAL = -6, OR_ENOCONV = -7 };
+enum { OR_OK = 0, OR_EINVAL = -1, OR_EUNBALANCED = -2, OR_ENONPHYSICAL = -6, OR_ENOCONV = -7,
+       OR_EBREAKDOWN = -8 };
 enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1 };
 enum { OR_HLLC = 0, OR_EXACT = 1 };
 /* nb27 entry for a father-level position outside an outflow boundary */
@@ -95,5 +96,14 @@ void or_mlp_forward(const double *theta, const double *x, int64_t n, double *y, 
 void or_mlp_backward(const double *theta, const double *x, const double *dy, int64_t n, double *act, double *grad);
 void or_adam_step(double *th, double *m, double *v, const double *grad, int64_t n, double lr,
                   double beta1, double beta2, double eps, int64_t t);
+
+/* Poisson solve on a box of nx*ny*nz cells, vectors indexed i + nx (j + ny k) (poisson.c) */
+enum { OR_PRECOND_NONE = 0, OR_PRECOND_IP = 1 };
+void or_poisson_apply_A(int nx, int ny, int nz, const double *x, double *y);
+void or_poisson_apply_Minv(int nx, int ny, int nz, int precond, const double *r, double *u);
+int or_cg(int nx, int ny, int nz, int precond, const double *b, double *x, double tol, int maxit,
+          double *eps, int *iters);
+int or_ppcg(int nx, int ny, int nz, int precond, const double *b, double *x, double tol, int maxit,
+            double *eps, int *iters);
 
 #endif

@@ -8,7 +8,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libamrhydro.so")
-SOURCES = ["octree.cu", "godunov_fp64.cu", "godunov_fp32.cu", "level_ops.cu", "mlp.cu"]
+SOURCES = ["octree.cu", "godunov_fp64.cu", "godunov_fp32.cu", "level_ops.cu", "mlp.cu", "ppcg.cu"]
 # per-file extra flags: the FP32 kernels use fast single-precision division / square root
 EXTRA = {"godunov_fp32.cu": ["--use_fast_math"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -24,16 +24,18 @@ def nvcc():
 
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
-    files.append(os.path.join(HERE, "..", "include", "amrhydro.h"))
+    inc = os.path.join(HERE, "..", "include")
+    files += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     return max(os.path.getmtime(f) for f in files)
 
 
 def source_hash():
-    """Hash of the CUDA sources: ties recorded profiler counters to a kernel version."""
+    """Hash of the sources the Godunov update kernels compile from: ties recorded profiler
+    counters of those kernels to a kernel version."""
     import hashlib
     h = hashlib.sha256()
     for f in sorted(os.listdir(CSRC)):
-        if f.endswith((".cu", ".cuh")):
+        if f.endswith((".cu", ".cuh")) and f.startswith(("godunov", "hydro_math", "common")):
             h.update(open(os.path.join(CSRC, f), "rb").read())
     return h.hexdigest()[:16]
 

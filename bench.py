@@ -552,6 +552,101 @@ def study_amr(args):
     return 0
 
 
+def study_poisson(args):
+    """Poisson solve of Sec. 2.3 on an N^3 Dirichlet box (Plummer-clump source): CG
+    (pipelined, no preconditioner) against PPCG (incomplete-Poisson preconditioner).
+    Per-iteration kernel time (events around a fixed number of fused iteration launches on
+    the launching stream), iterations and time to eps = 1e-4 (Eq. 3), roofline of the
+    iteration kernel against HBM and the FP64 pipe, and the oracle on the host cores."""
+    import numpy as np
+    import torch
+    from paper_2411_14631_gb300 import build, abi
+    build.build()
+    from paper_2411_14631_gb300 import poisson as PS
+    from paper_2411_14631_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    N = args.poisson_n
+    shape = (N, N, N)
+    n = N ** 3
+    b_h = W.poisson_rhs(N)
+    b = torch.tensor(b_h, device="cuda:0")
+    stream = torch.cuda.Stream()
+    hbm, peak_kind = peaks()
+    # FP64 pipe: 1.25 TFLOP/s nominal = 0.625e12 DFMA/s, i.e. 2 DP instructions per clock
+    # per SM at 2.07 GHz on 152 SMs
+    fp64_peak = 152 * 2 * 2.07e9
+    # algorithmic DP instructions and HBM bytes per cell and iteration
+    alg = {abi.PRECOND_IP: (23, 16 * 8), abi.PRECOND_NONE: (14, 12 * 8)}
+    out = {"study": "Poisson solve on a %d^3 Dirichlet box, CG vs PPCG (Sec. 2.3, Fig. 4)" % N,
+           "data": "synthetic: 64 Plummer clumps (core 0.005, contrast 1e4, truncated at r = 0.1), "
+                   "b = -4 pi h^2 (rho - mean)", "cells": n, "tol": 1e-4,
+           "l2": "inputs larger than L2 (8 FP64 vectors of %d MB)" % (n * 8 >> 20)}
+    clk = Clocks(0)
+    res = {}
+    K = args.steps if args.steps > 10 else 50
+    for name, pc in (("cg", abi.PRECOND_NONE), ("ppcg", abi.PRECOND_IP)):
+        best = None
+        for ty in (8, 16):
+            for seg in (0, 16, 32, 64):
+                s = PS.PPCG(shape, precond=pc, tol=0.0, max_iter=K + 10, tile_y=ty, seg=seg)
+                x = torch.zeros(n, dtype=torch.float64, device="cuda:0")
+                with torch.cuda.stream(stream):
+                    s.start(b, x, stream)
+                    s.iterate(x, 5, stream)            # warm-up
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    s.iterate(x, K, stream)
+                    e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1) / K
+                if best is None or ms < best[0]:
+                    best = (ms, ty, seg)
+                del s, x
+        ms, ty, seg = best
+        # time to solution at the best launch shape, clocks sampled meanwhile
+        s = PS.PPCG(shape, precond=pc, tol=1e-4, max_iter=5000, tile_y=ty, seg=seg)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda:0")
+        s.solve(b, x.clone(), stream)             # warm-up solve
+        torch.cuda.synchronize()
+        clk.start()
+        with torch.cuda.stream(stream):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, eps, info = s.solve(b, x, stream)
+            e1.record(stream)
+        stream.synchronize()
+        clocks = clk.stop()
+        clk = Clocks(0)
+        solve_ms = e0.elapsed_time(e1)
+        ops, nbytes = alg[pc]
+        res[name] = {"iterations_to_tol": info.iters, "status": info.status, "eps_final": info.eps,
+                     "solve_ms": solve_ms, "iteration_ms": ms, "tile_y": ty, "seg": seg,
+                     "cell_iterations_per_s": n / (ms * 1e-3),
+                     "hbm": {"algorithmic_bytes_per_cell": nbytes, "achieved_gbs": n * nbytes / (ms * 1e-3) / 1e9,
+                             "peak_gbs": hbm, "peak_kind": peak_kind,
+                             "frac": n * nbytes / (ms * 1e-3) / 1e9 / hbm},
+                     "fp64": {"algorithmic_dp_instr_per_cell": ops, "achieved_gops": n * ops / (ms * 1e-3) / 1e9,
+                              "peak_gops": fp64_peak / 1e9, "peak_kind": "derived from the nominal 1.25 TFLOP/s",
+                              "frac": n * ops / (ms * 1e-3) / fp64_peak},
+                     "launches_per_iteration": 1, "clocks": clocks,
+                     "eps_history_every_10": [float(e) for e in eps[::10]]}
+        del s, x
+    res["iteration_ratio_cg_over_ppcg"] = res["cg"]["iterations_to_tol"] / res["ppcg"]["iterations_to_tol"]
+    res["time_ratio_cg_over_ppcg"] = res["cg"]["solve_ms"] / res["ppcg"]["solve_ms"]
+    out.update(res)
+    if not args.skip_cpu:
+        import oracle as O
+        O.build()
+        t0 = time.perf_counter()
+        it = 20
+        O.ppcg(shape, b_h, precond=O.PRECOND_IP, tol=0.0, maxit=it)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n * it / dt, "unit": "cell-iterations/s", "cores": 1, "kind": "oracle",
+                               "sample": "oracle PPCG, %d iterations of the %d^3 solve (incl. set-up)" % (it, N)}
+    print(json.dumps(out))
+    return 0
+
+
 def leaf_count(tree):
     return tree.leaf_cells()
 
@@ -566,7 +661,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--study", default=None, choices=["surrogate", "sedov", "amr"])
+    ap.add_argument("--study", default=None, choices=["surrogate", "sedov", "amr", "poisson"])
+    ap.add_argument("--poisson-n", type=int, default=256)
     ap.add_argument("--harvest", type=int, default=10_000_000)
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--tol", type=float, default=0.02)
@@ -578,6 +674,8 @@ def main():
         return study_sedov(args)
     if args.study == "amr":
         return study_amr(args)
+    if args.study == "poisson":
+        return study_poisson(args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
 

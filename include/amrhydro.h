@@ -48,7 +48,9 @@ typedef enum {
     AMR_ECUDA = -4,         /* a CUDA runtime call failed */
     AMR_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
     AMR_ENONPHYSICAL = -6,  /* vacuum in an exact Riemann problem (HLLC flux used instead) */
-    AMR_ENOCONV = -7        /* exact Riemann Newton iteration did not converge (HLLC used) */
+    AMR_ENOCONV = -7,       /* an iteration did not converge: the exact Riemann Newton iteration
+                               (HLLC used instead), or a Poisson solve within its iteration cap */
+    AMR_EBREAKDOWN = -8     /* a Poisson solve met a step length that is not positive and finite */
 } amr_status;
 
 enum { AMR_BC_PERIODIC = 0, AMR_BC_OUTFLOW = 1 };

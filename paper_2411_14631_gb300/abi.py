@@ -10,16 +10,19 @@ LIB_PATH = os.path.join(HERE, "libamrhydro.so")
 MAXLEV = 21
 NCOUNTERS = 8
 
-OK, EINVAL, EUNBALANCED, ECAPACITY, ECUDA, ETIMEOUT, ENONPHYSICAL, ENOCONV = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, EUNBALANCED, ECAPACITY, ECUDA, ETIMEOUT, ENONPHYSICAL, ENOCONV, EBREAKDOWN = 0, -1, -2, -3, -4, -5, -6, -7, -8
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 RIEMANN_HLLC, RIEMANN_EXACT, RIEMANN_MLP = 0, 1, 2
 PREC_FP64, PREC_FP32 = 0, 1
+PRECOND_NONE, PRECOND_IP = 0, 1
+OP_A, OP_MINV = 0, 1
 
 EXPORTS = ["amr_build_octree_query", "amr_build_octree", "hydro_init_from_prim", "hydro_prim_of_state",
            "hydro_courant", "hydro_godunov_level", "hydro_flux_reg_bytes", "hydro_reflux_level", "hydro_step",
            "amr_get_status", "amr_status_string", "hydro_step_static_scratch", "hydro_harvest_faces",
            "mlp_nparams", "mlp_packed_bytes", "mlp_scratch_bytes", "mlp_pack", "mlp_make_dataset", "mlp_forward",
-           "mlp_grad", "mlp_train_step"]
+           "mlp_grad", "mlp_train_step",
+           "ppcg_workspace_bytes", "poisson_apply", "ppcg_start", "ppcg_iterate", "ppcg_poll", "ppcg_solve"]
 MLP_NPARAMS = 8962
 STATIC_REG_MAX_OCTS = 131072
 
@@ -46,6 +49,17 @@ class AmrTree(C.Structure):
                 ("tile_slot", C.c_void_p * 2), ("n_inst", C.c_int32), ("inst_n", C.c_void_p), ("inst_dx", C.c_void_p),
                 ("inst_oct_off", C.c_void_p), ("tile_inst", C.c_void_p * 2), ("grid_level", C.c_int32),
                 ("grid", C.c_void_p), ("col_work", C.c_int64), ("inst_col_off", C.c_void_p)]
+
+
+class PpcgParams(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("precond", C.c_int32),
+                ("tol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32), ("tile_y", C.c_int32),
+                ("seg", C.c_int32)]
+
+
+class PpcgInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("done", C.c_int32), ("status", C.c_int32), ("pad", C.c_int32),
+                ("eps", C.c_double)]
 
 
 _lib = None
@@ -84,11 +98,21 @@ def lib():
     L.mlp_forward.argtypes = [P, P, P, C.c_int64, P]
     L.mlp_grad.argtypes = [P, P, P, C.c_int64, P, P, S, P]
     L.mlp_train_step.argtypes = [P, P, P, P, P, P, C.c_int64, C.c_float, C.c_int64, P, P, S, P]
+    PG = C.POINTER(PpcgParams)
+    I = C.c_int32
+    L.ppcg_workspace_bytes.argtypes = [I, I, I]
+    L.ppcg_workspace_bytes.restype = S
+    L.poisson_apply.argtypes = [I, I, I, I, P, P, P]
+    L.ppcg_start.argtypes = [PG, P, P, P, S, P, P]
+    L.ppcg_iterate.argtypes = [PG, P, P, S, P, I, P]
+    L.ppcg_poll.argtypes = [P, C.POINTER(PpcgInfo), P]
+    L.ppcg_solve.argtypes = [PG, P, P, P, S, P, C.POINTER(PpcgInfo), P]
     L.amr_get_status.argtypes = [PP, P, P]
     L.amr_status_string.argtypes = [C.c_int]
     L.amr_status_string.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("hydro_flux_reg_bytes", "amr_status_string", "mlp_packed_bytes", "mlp_scratch_bytes"):
+        if name not in ("hydro_flux_reg_bytes", "amr_status_string", "mlp_packed_bytes", "mlp_scratch_bytes",
+                        "ppcg_workspace_bytes"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L

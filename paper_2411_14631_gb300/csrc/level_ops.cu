@@ -345,7 +345,8 @@ extern "C" const char *amr_status_string(int s)
     case AMR_ECUDA: return "CUDA runtime error";
     case AMR_ETIMEOUT: return "device wait timed out";
     case AMR_ENONPHYSICAL: return "vacuum in an exact Riemann problem";
-    case AMR_ENOCONV: return "exact Riemann solver did not converge";
+    case AMR_ENOCONV: return "iteration did not converge";
+    case AMR_EBREAKDOWN: return "Krylov iteration broke down";
     default: return "unknown status";
     }
 }

@@ -16,6 +16,8 @@ conditions are not available, these synthetic fields stand in for them):
                       refined by a quasi-Lagrangian mass threshold, 2:1 balanced.
 * ``sedov``        -- point blast, E = 1 deposited in one cell, rho = 1, p = 1e-5.
 * ``random_tree``  -- tiny random balanced octrees for table tests.
+* ``poisson_rhs``  -- right-hand side of the gravity solve on an N^3 Dirichlet box: the
+                      plummer clumps (truncated at r = 0.1) as the source, -4 pi h^2 (rho - mean).
 """
 import itertools
 
@@ -294,3 +296,32 @@ def batch_prims(sizes, per_box_lex):
         W = per_box_lex(int(N))
         out.append(W[:, box_batch_to_lex(int(N))])
     return np.concatenate(out, axis=1)
+
+
+POISSON_CLUMP_RMAX = 0.1
+
+
+def poisson_density(N, nclump=64, seed=3, a=PLUMMER_A, contrast=PLUMMER_CONTRAST):
+    """rho = 1 + sum of Plummer clumps (as plummer_density, periodic minimum image), each
+    truncated at r = POISSON_CLUMP_RMAX, at the cell centres of an N^3 box; the array is
+    indexed i + N (j + N k)."""
+    centres = plummer_centres(nclump, seed)
+    rho = np.ones((N, N, N))                      # [k, j, i]
+    R = int(np.ceil(POISSON_CLUMP_RMAX * N))
+    off = np.arange(-R, R + 1)
+    for c in centres:
+        ic = np.floor(c * N).astype(np.int64)
+        idx = [(ic[d] + off) % N for d in range(3)]
+        dd = [((idx[d] + 0.5) / N - c[d]) for d in range(3)]
+        dd = [x - np.round(x) for x in dd]
+        r2 = dd[2][:, None, None] ** 2 + dd[1][None, :, None] ** 2 + dd[0][None, None, :] ** 2
+        val = np.where(r2 <= POISSON_CLUMP_RMAX ** 2, contrast * (1.0 + r2 / (a * a)) ** -2.5, 0.0)
+        rho[np.ix_(idx[2], idx[1], idx[0])] += val
+    return rho.ravel()
+
+
+def poisson_rhs(N, seed=0, nclump=64):
+    """b = -4 pi h^2 (rho - mean rho), h = 1/N, G = 1: the source of A x = b with A the
+    7-point -h^2 Laplacian and homogeneous Dirichlet boundaries (box of N^3 cells)."""
+    rho = poisson_density(N, nclump=nclump, seed=3 + seed)
+    return -4.0 * np.pi * (rho - rho.mean()) / float(N * N)

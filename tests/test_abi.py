@@ -78,3 +78,34 @@ def test_query_is_host_only_and_validates(built):
     g.bc[0] = 1
     assert abi.lib().amr_build_octree_query(C.byref(g), bad.ctypes.data_as(C.c_void_p), bad.shape[0],
                                             C.byref(tb), C.byref(wb)) == abi.EINVAL
+
+
+def test_poisson_entry_points_validate_on_host(built, tmp_path):
+    """The Poisson calls check their arguments before any CUDA call; the ctypes structs
+    have the C layout."""
+    import ctypes as C
+    from paper_2411_14631_gb300 import abi
+    L = abi.lib()
+    n = 37 * 21 * 13
+    nb = L.ppcg_workspace_bytes(37, 21, 13)
+    assert nb >= 8 * n * 8 and L.ppcg_workspace_bytes(0, 21, 13) == 0
+    assert L.poisson_apply(37, 21, 13, 5, C.c_void_p(256), C.c_void_p(512), None) == abi.EINVAL
+    assert L.poisson_apply(0, 21, 13, abi.OP_A, C.c_void_p(256), C.c_void_p(512), None) == abi.EINVAL
+    prm = abi.PpcgParams(37, 21, 13, abi.PRECOND_IP, 1e-4, 10, 0, 0, 0)
+    w = C.c_void_p(1 << 20)
+    assert L.ppcg_start(C.byref(prm), w, w, C.c_void_p((1 << 20) + 8), nb, None, None) == abi.EINVAL  # misaligned
+    assert L.ppcg_start(C.byref(prm), w, w, w, nb - 1, None, None) == abi.ECAPACITY
+    for bad in (dict(precond=3), dict(tol=-1.0), dict(max_iter=-1), dict(tile_y=12), dict(seg=2)):
+        p2 = abi.PpcgParams(37, 21, 13, abi.PRECOND_IP, 1e-4, 10, 0, 0, 0)
+        for k, v in bad.items():
+            setattr(p2, k, v)
+        assert L.ppcg_iterate(C.byref(p2), w, w, nb, None, 1, None) == abi.EINVAL, bad
+    src = tmp_path / "pp.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ppcg.h"\n'
+                   'int main(){printf("%zu %zu %zu %zu\\n", sizeof(ppcg_params), sizeof(ppcg_info),'
+                   ' offsetof(ppcg_params, seg), offsetof(ppcg_info, eps));}\n')
+    exe = tmp_path / "pp"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [C.sizeof(abi.PpcgParams), C.sizeof(abi.PpcgInfo), abi.PpcgParams.seg.offset,
+                   abi.PpcgInfo.eps.offset]

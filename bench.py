@@ -586,8 +586,8 @@ def study_poisson(args):
     K = args.steps if args.steps > 10 else 50
     for name, pc in (("cg", abi.PRECOND_NONE), ("ppcg", abi.PRECOND_IP)):
         best = None
-        for ty in (8, 16):
-            for seg in (0, 16, 32, 64):
+        for ty in ((8, 16) if args.poisson_tile_y == 0 else (args.poisson_tile_y,)):
+            for seg in ((0, 16, 32, 64) if args.poisson_seg < 0 else (args.poisson_seg,)):
                 s = PS.PPCG(shape, precond=pc, tol=0.0, max_iter=K + 10, tile_y=ty, seg=seg)
                 x = torch.zeros(n, dtype=torch.float64, device="cuda:0")
                 with torch.cuda.stream(stream):
@@ -663,6 +663,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--study", default=None, choices=["surrogate", "sedov", "amr", "poisson"])
     ap.add_argument("--poisson-n", type=int, default=256)
+    ap.add_argument("--poisson-tile-y", type=int, default=0, help="8 or 16; 0 tries both")
+    ap.add_argument("--poisson-seg", type=int, default=-1, help="z planes per block; -1 tries several")
     ap.add_argument("--harvest", type=int, default=10_000_000)
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--tol", type=float, default=0.02)

@@ -396,11 +396,13 @@ def study_surrogate(args):
 
     ref = run(H.Params(GAMMA, cfl=CFL, riemann=abi.RIEMANN_EXACT))
     paths = {}
-    for name, riemann, prec in (("exact_fp32", abi.RIEMANN_EXACT, abi.PREC_FP32),
-                                ("mlp_fallback_fp32", abi.RIEMANN_MLP, abi.PREC_FP32),
-                                ("hllc_fp32", abi.RIEMANN_HLLC, abi.PREC_FP32),
-                                ("hllc_fp64_plain", abi.RIEMANN_HLLC, abi.PREC_FP64)):
-        prm = H.Params(GAMMA, cfl=CFL, riemann=riemann, precision=prec)
+    for name, riemann, prec, tonly in (("exact_fp32", abi.RIEMANN_EXACT, abi.PREC_FP32, False),
+                                       ("exact_fp32_tiles", abi.RIEMANN_EXACT, abi.PREC_FP32, True),
+                                       ("mlp_fallback_fp32", abi.RIEMANN_MLP, abi.PREC_FP32, False),
+                                       ("mlp_seeded_newton_fp32", abi.RIEMANN_MLP_SEEDED, abi.PREC_FP32, False),
+                                       ("hllc_fp32", abi.RIEMANN_HLLC, abi.PREC_FP32, False),
+                                       ("hllc_fp64_plain", abi.RIEMANN_HLLC, abi.PREC_FP64, False)):
+        prm = H.Params(GAMMA, cfl=CFL, riemann=riemann, precision=prec, tiles_only=tonly)
         prm.c.mlp_weights = sur.packed.data_ptr()
         prm.c.mlp_resid_tol = args.tol
         u = run(prm)
@@ -416,6 +418,14 @@ def study_surrogate(args):
             rec["fallbacks"] = cntr[1]
             rec["fallback_rate"] = cntr[1] / max(1, tot)
             rec["tol"] = args.tol
+        if riemann == abi.RIEMANN_MLP_SEEDED:
+            rec["faces_seeded"] = cntr[0]
+            rec["cold_starts"] = cntr[1]
+        if cntr[3] > 0:
+            rec["newton_iterations_per_solve"] = cntr[2] / cntr[3]
+            rec["newton_solves"] = cntr[3]
+        if tonly:
+            rec["kernel"] = "tile kernel for every level (the Newton counters are kept there)"
         paths[name] = rec
     out["paths"] = paths
     out["reference"] = "FP64 exact-solver path on the GPU (equal to the oracle within 1e-12), 10 steps, fixed dt"
@@ -586,8 +596,9 @@ def study_poisson(args):
     K = args.steps if args.steps > 10 else 50
     for name, pc in (("cg", abi.PRECOND_NONE), ("ppcg", abi.PRECOND_IP)):
         best = None
+        sweep = {}
         for ty in ((8, 16) if args.poisson_tile_y == 0 else (args.poisson_tile_y,)):
-            for seg in ((0, 16, 32, 64) if args.poisson_seg < 0 else (args.poisson_seg,)):
+            for seg in ((0, 14, 16, 22, 32, 43, 64) if args.poisson_seg < 0 else (args.poisson_seg,)):
                 s = PS.PPCG(shape, precond=pc, tol=0.0, max_iter=K + 10, tile_y=ty, seg=seg)
                 x = torch.zeros(n, dtype=torch.float64, device="cuda:0")
                 with torch.cuda.stream(stream):
@@ -599,6 +610,7 @@ def study_poisson(args):
                     e1.record(stream)
                 stream.synchronize()
                 ms = e0.elapsed_time(e1) / K
+                sweep["%d/%d" % (ty, seg)] = round(ms, 4)
                 if best is None or ms < best[0]:
                     best = (ms, ty, seg)
                 del s, x
@@ -621,6 +633,7 @@ def study_poisson(args):
         ops, nbytes = alg[pc]
         res[name] = {"iterations_to_tol": info.iters, "status": info.status, "eps_final": info.eps,
                      "solve_ms": solve_ms, "iteration_ms": ms, "tile_y": ty, "seg": seg,
+                     "iteration_ms_by_tile_y_seg": sweep,
                      "cell_iterations_per_s": n / (ms * 1e-3),
                      "hbm": {"algorithmic_bytes_per_cell": nbytes, "achieved_gbs": n * nbytes / (ms * 1e-3) / 1e9,
                              "peak_gbs": hbm, "peak_kind": peak_kind,

@@ -54,7 +54,7 @@ typedef enum {
 } amr_status;
 
 enum { AMR_BC_PERIODIC = 0, AMR_BC_OUTFLOW = 1 };
-enum { AMR_RIEMANN_HLLC = 0, AMR_RIEMANN_EXACT = 1, AMR_RIEMANN_MLP = 2 };
+enum { AMR_RIEMANN_HLLC = 0, AMR_RIEMANN_EXACT = 1, AMR_RIEMANN_MLP = 2, AMR_RIEMANN_MLP_SEEDED = 3 };
 enum { AMR_PREC_FP64 = 0, AMR_PREC_FP32 = 1 };
 
 #define AMR_MAXLEV 21
@@ -77,11 +77,15 @@ typedef struct {
    tile: 1 or 2 = depth of the oct tiles a CTA updates (8 or 64 octs), 0 = default;
    tiles_only: 0 = the deepest complete level is updated by the z-column kernel (the
    same arithmetic per cell as the tiles, less ghost work), 1 = tiles for every level;
-   mlp_weights: device pointer to the surrogate's weights (AMR_RIEMANN_MLP only);
+   mlp_weights: device pointer to the surrogate's weights (AMR_RIEMANN_MLP and
+   AMR_RIEMANN_MLP_SEEDED only);
    mlp_resid_tol: acceptance threshold of the surrogate's residual check;
    d_status: device int32 error word (may be NULL); d_counters: device uint64
-   counters[AMR_NCOUNTERS] (may be NULL): [0] faces solved by the surrogate,
-   [1] surrogate fallbacks to the exact solver, [2] exact-solver failures. */
+   counters[AMR_NCOUNTERS] (may be NULL), accumulated over calls: [0] faces solved by the
+   surrogate (AMR_RIEMANN_MLP) or whose Newton solve it seeded (AMR_RIEMANN_MLP_SEEDED),
+   [1] faces where the surrogate's answer was not used (fallback to a cold Newton start),
+   [2] Newton iterations and [3] Newton solves made by the tile kernel's exact solver
+   and by both surrogate modes (the z-column kernel does not count). */
 typedef struct {
     double gamma, cfl, rho_floor, p_floor;
     int32_t riemann, precision, tile, tiles_only;
@@ -228,7 +232,10 @@ amr_status hydro_step_static_scratch(const amr_tree *tree, const hydro_params *p
    (AMR_PREC_FP32 only) the Godunov kernel evaluates the network at every face, accepts
    (p_star, u_star) when p_star > 0 and both |f(p_star)| and the velocity relation are
    within mlp_resid_tol * (c_L + c_R), and otherwise solves the face exactly; counters[0]
-   and [1] count accepted faces and fallbacks. */
+   and [1] count accepted faces and fallbacks.  With AMR_RIEMANN_MLP_SEEDED the network's
+   p_star is instead the initial guess of the exact Newton iteration at every face (the
+   linearised guess where the prediction is unusable), so every face gets the exact
+   solver's answer to its tolerance and the network only saves iterations. */
 #define AMR_MLP_NPARAMS 8962
 int mlp_nparams(void);
 /* Bytes of the packed BF16 weight block (device, 16-byte aligned) used by every kernel. */

@@ -45,7 +45,7 @@ typedef struct {
     double tol;               /* stop at the first i >= 1 with eps_i <= tol; >= 0 */
     int32_t max_iter;         /* >= 0 */
     int32_t check_every;      /* ppcg_solve: iterations launched between host checks (0: 16) */
-    int32_t tile_y;           /* rows of the 32-wide tile of one thread block: 8 or 16 (0: 16) */
+    int32_t tile_y;           /* rows of the 32-wide tile of one thread block: 8 or 16 (0: 8) */
     int32_t seg;              /* z planes one thread block marches through (0: chosen; else >= 4) */
 } ppcg_params;
 

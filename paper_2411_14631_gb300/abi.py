@@ -12,7 +12,7 @@ NCOUNTERS = 8
 
 OK, EINVAL, EUNBALANCED, ECAPACITY, ECUDA, ETIMEOUT, ENONPHYSICAL, ENOCONV, EBREAKDOWN = 0, -1, -2, -3, -4, -5, -6, -7, -8
 BC_PERIODIC, BC_OUTFLOW = 0, 1
-RIEMANN_HLLC, RIEMANN_EXACT, RIEMANN_MLP = 0, 1, 2
+RIEMANN_HLLC, RIEMANN_EXACT, RIEMANN_MLP, RIEMANN_MLP_SEEDED = 0, 1, 2, 3
 PREC_FP64, PREC_FP32 = 0, 1
 PRECOND_NONE, PRECOND_IP = 0, 1
 OP_A, OP_MINV = 0, 1

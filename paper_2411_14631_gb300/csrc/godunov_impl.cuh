@@ -49,6 +49,7 @@ struct GArgs {
     unsigned long long *counters;
     const void *mlp;          // packed surrogate weights (RS == AMR_RIEMANN_MLP)
     float mlp_tol;            // residual acceptance threshold
+    int32_t mlp_seed;         // 1: the network's p* seeds Newton at every face (no acceptance test)
     double *harvest;          // if set: sampled face states [cap][6] are written, u_new is not
     int64_t harvest_cap, harvest_stride;
     unsigned long long *harvest_count;
@@ -162,7 +163,8 @@ __device__ __forceinline__ void face_states(const Smem<R, D, RS> &sm, int r0, co
 
 template <typename R, int D, int RS, int DIR>
 __device__ __forceinline__ void face_flux(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>::NF], int r0, const Prm<R> &pr,
-                                          int32_t *status, const GArgs &a, int64_t tile)
+                                          int32_t *status, const GArgs &a, int64_t tile, unsigned &n_it,
+                                          unsigned &n_solve)
 {
     using G = Geo<D>;
     const int fa = r0 % (G::CI + 1), t1 = (r0 / (G::CI + 1)) % G::CI, t2 = r0 / ((G::CI + 1) * G::CI);
@@ -205,7 +207,10 @@ __device__ __forceinline__ void face_flux(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>
     if (RS == AMR_RIEMANN_EXACT) {
         R ps, us;
         const R tol = sizeof(R) == 8 ? R(1e-14) : R(1e-6);
-        const int e = exact_star(WL, WR, pr.gamma, tol, 50, ps, us);
+        int its;
+        const int e = exact_star(WL, WR, pr.gamma, tol, 50, ps, us, R(-1), &its);
+        n_it += its;
+        ++n_solve;
         if (e == 0) {
             R W0[NV], U0[NV];
             exact_sample0(WL, WR, pr.gamma, ps, us, W0);
@@ -233,7 +238,8 @@ __device__ __forceinline__ void face_flux(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>
 // All 32 lanes of the warp take part; lanes past the last face carry a dummy problem.
 template <typename R, int D, int RS>
 __device__ __forceinline__ void mlp_faces(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>::NF], const Prm<R> &pr,
-                                          const GArgs &a, unsigned &n_acc, unsigned &n_fb)
+                                          const GArgs &a, unsigned &n_acc, unsigned &n_fb, unsigned &n_it,
+                                          unsigned &n_solve)
 {
     using G = Geo<D>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -272,7 +278,7 @@ __device__ __forceinline__ void mlp_faces(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>
         const bool vac = R(2) * (cL + cR) / (g - R(1)) <= uR - uL;
         const R ps = pref * exp(y0), us = ubar + cref * y1;
         bool ok = !vac && isfinite(ps) && ps > R(0) && isfinite(us);
-        if (ok) {
+        if (ok && !a.mlp_seed) {
             R fL, dfL, fR, dfR;
             side_f(ps, rL, pL, cL, g, fL, dfL);
             side_f(ps, rR, pR, cR, g, fR, dfR);
@@ -280,13 +286,20 @@ __device__ __forceinline__ void mlp_faces(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>
             ok = fabs(fL + fR + (uR - uL)) <= tolc && fabs(us - (R(0.5) * (uL + uR) + R(0.5) * (fR - fL))) <= tolc;
         }
         R Fn[NV], W0[NV], U0[NV];
-        if (ok) {
+        if (ok && !a.mlp_seed) {
             exact_sample0(WL, WR, g, ps, us, W0);
             flux_normal(W0, g, Fn, U0);
         } else {
+            // exact Newton solve: seeded by the network's p* when it is usable (seeded
+            // mode), from the linearised guess otherwise
             R ps2, us2;
             const R tol = sizeof(R) == 8 ? R(1e-14) : R(1e-6);
-            const int e = exact_star(WL, WR, g, tol, 50, ps2, us2);
+            int its;
+            const int e = exact_star(WL, WR, g, tol, 50, ps2, us2, ok ? ps : R(-1), &its);
+            if (valid) {
+                n_it += its;
+                ++n_solve;
+            }
             if (e == 0) {
                 exact_sample0(WL, WR, g, ps2, us2, W0);
                 flux_normal(W0, g, Fn, U0);
@@ -295,6 +308,7 @@ __device__ __forceinline__ void mlp_faces(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>
                 hllc(WL, WR, g, Fn);
             }
         }
+        // accepted (seeded) faces and fallbacks (cold starts)
         const unsigned acc = __ballot_sync(0xffffffffu, ok && valid), fb = __ballot_sync(0xffffffffu, !ok && valid);
         n_acc += __popc(acc);
         n_fb += __popc(fb);
@@ -326,6 +340,7 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
     const R cflR = to_work<R>(a.cfl);
 
     unsigned n_acc = 0, n_fb = 0;   // surrogate: accepted faces, fallbacks (counted by lane 0)
+    unsigned n_it = 0, n_solve = 0; // Newton iterations and Newton solves of this thread
     for (int64_t t = a.t_begin + blockIdx.x; t < a.t_end; t += gridDim.x) {
         // ---- level of this tile and its geometry
         const int32_t root = a.tile_root[t];
@@ -439,13 +454,13 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
 
         // ---- phase 3: Riemann problem at every face touching an updated cell
         if constexpr (RS == AMR_RIEMANN_MLP) {
-            mlp_faces<R, D, RS>(sm, sF, pr, a, n_acc, n_fb);
+            mlp_faces<R, D, RS>(sm, sF, pr, a, n_acc, n_fb, n_it, n_solve);
         } else {
             for (int f = tid; f < 3 * G::NF; f += blockDim.x) {
                 const int d = f / G::NF, r0 = f - d * G::NF;
-                if (d == 0) face_flux<R, D, RS, 0>(sm, sF, r0, pr, a.status, a, t);
-                else if (d == 1) face_flux<R, D, RS, 1>(sm, sF, r0, pr, a.status, a, t);
-                else face_flux<R, D, RS, 2>(sm, sF, r0, pr, a.status, a, t);
+                if (d == 0) face_flux<R, D, RS, 0>(sm, sF, r0, pr, a.status, a, t, n_it, n_solve);
+                else if (d == 1) face_flux<R, D, RS, 1>(sm, sF, r0, pr, a.status, a, t, n_it, n_solve);
+                else face_flux<R, D, RS, 2>(sm, sF, r0, pr, a.status, a, t, n_it, n_solve);
             }
         }
         __syncthreads();
@@ -559,6 +574,13 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
         atomicAdd(a.counters + 0, (unsigned long long)n_acc);
         atomicAdd(a.counters + 1, (unsigned long long)n_fb);
     }
+    if (RS != AMR_RIEMANN_HLLC && a.counters) {
+        const unsigned it_w = __reduce_add_sync(0xffffffffu, n_it), so_w = __reduce_add_sync(0xffffffffu, n_solve);
+        if ((tid & 31) == 0 && so_w) {
+            atomicAdd(a.counters + 2, (unsigned long long)it_w);
+            atomicAdd(a.counters + 3, (unsigned long long)so_w);
+        }
+    }
 }
 
 template <typename R, int D, int RS>
@@ -582,17 +604,18 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
 {
     int depth = p->tile == 0 ? 1 : p->tile;
     if (depth != 1 && depth != 2) return AMR_EINVAL;
+    const bool mlp_like = p->riemann == AMR_RIEMANN_MLP || p->riemann == AMR_RIEMANN_MLP_SEEDED;
     if (depth == 2 && sizeof(R) == 8) return AMR_EINVAL;   // an FP64 12^3-cell stencil does not fit in smem
     if (t->n_inst > 0) {
         // batch mode: every box in one launch (z-column kernel when every box is a multiple of
         // 16 cells, else tiles)
         if (level != -1) return AMR_EINVAL;
-        if (!p->tiles_only && p->riemann != AMR_RIEMANN_MLP && t->col_work > 0)
+        if (!p->tiles_only && !mlp_like && t->col_work > 0)
             return p->riemann == AMR_RIEMANN_EXACT
                        ? launch_col<R, AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, st)
                        : launch_col<R, AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, st);
         if (depth == 2 && t->tile_off[1][1] == 0) depth = 1;            // some box is not a multiple of 8
-        if (p->riemann == AMR_RIEMANN_MLP) depth = 1;
+        if (mlp_like) depth = 1;
         const int d = depth;
         GArgs a;
         a.tv = make_view(t);
@@ -606,11 +629,11 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
         a.u_old = u_old; a.u_new = u_new; a.reg = nullptr; a.dt = dt; a.dt_next = dt_next;
         a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
         a.status = p->d_status; a.counters = p->d_counters;
-        a.mlp = p->mlp_weights; a.mlp_tol = p->mlp_resid_tol;
+        a.mlp = p->mlp_weights; a.mlp_tol = p->mlp_resid_tol; a.mlp_seed = p->riemann == AMR_RIEMANN_MLP_SEEDED;
         a.harvest = nullptr; a.harvest_cap = 0; a.harvest_stride = 1; a.harvest_count = nullptr;
         const int64_t nt = a.t_end;
         constexpr int D2 = 2 - (sizeof(R) == 8);
-        if (p->riemann == AMR_RIEMANN_MLP) {
+        if (mlp_like) {
             if (sizeof(R) == 8 || !p->mlp_weights) return AMR_EINVAL;
             return launch<R, 1, AMR_RIEMANN_MLP>(a, nt, st);
         }
@@ -625,7 +648,7 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
     // the deepest complete level goes to the z-column kernel (bitwise the same per cell);
     // the levels below and above it to the tile kernel
     const int gl = t->grid_level;
-    if (!p->tiles_only && p->riemann != AMR_RIEMANN_MLP && t->grid && gl >= 3 && gl >= l0 && gl <= l1) {
+    if (!p->tiles_only && !mlp_like && t->grid && gl >= 3 && gl >= l0 && gl <= l1) {
         const amr_status r = p->riemann == AMR_RIEMANN_EXACT
                                  ? launch_col<R, AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, st)
                                  : launch_col<R, AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, st);
@@ -659,13 +682,14 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
         const int64_t nt = a.t_end - a.t_begin;
         a.mlp = p->mlp_weights;
         a.mlp_tol = p->mlp_resid_tol;
+        a.mlp_seed = p->riemann == AMR_RIEMANN_MLP_SEEDED;
         a.harvest = nullptr;
         a.harvest_cap = 0;
         a.harvest_stride = 1;
         a.harvest_count = nullptr;
         constexpr int D2 = 2 - (sizeof(R) == 8);
         amr_status r;
-        if (p->riemann == AMR_RIEMANN_MLP) {
+        if (mlp_like) {
             if (sizeof(R) == 8 || !p->mlp_weights) return AMR_EINVAL;   // the surrogate runs in the FP32 path
             // the network's fragments need the register budget of 128-thread CTAs: depth-1 tiles
             if (d != 1) {
@@ -704,7 +728,7 @@ inline amr_status harvest_impl(const amr_tree *t, const hydro_params *p, const d
     a.u_old = u; a.u_new = nullptr; a.reg = nullptr; a.dt = dt; a.dt_next = nullptr;
     a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
     a.status = p->d_status; a.counters = nullptr;
-    a.mlp = nullptr; a.mlp_tol = 0.0f;
+    a.mlp = nullptr; a.mlp_tol = 0.0f; a.mlp_seed = 0;
     a.harvest = out; a.harvest_cap = cap; a.harvest_stride = stride; a.harvest_count = count;
     return launch<double, 1, AMR_RIEMANN_HLLC>(a, a.t_end - a.t_begin, st);
 }

@@ -129,17 +129,21 @@ __device__ __forceinline__ void side_f(R p, R rK, R pK, R cK, R g, R &f, R &df)
 }
 
 // Exact Riemann problem (Toro Ch. 4).  Returns 0, AMR_ENONPHYSICAL (vacuum) or
-// AMR_ENOCONV; on failure the caller uses HLLC.
+// AMR_ENOCONV; on failure the caller uses HLLC.  Newton starts from p0 when p0 > 0 (a
+// learned prediction), else from the linearised (PVRS) guess; *iters receives the
+// iterations made.
 template <typename R>
-__device__ int exact_star(const R WL[NV], const R WR[NV], R g, R tol, int maxit, R &ps, R &us)
+__device__ int exact_star(const R WL[NV], const R WR[NV], R g, R tol, int maxit, R &ps, R &us, R p0 = R(-1),
+                          int *iters = nullptr)
 {
+    if (iters) *iters = 0;
     const R rL = WL[0], uL = WL[1], pL = WL[4];
     const R rR = WR[0], uR = WR[1], pR = WR[4];
     const R cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
     const R du = uR - uL;
     if (R(2) * (cL + cR) / (g - R(1)) <= du) return AMR_ENONPHYSICAL;
     const R eps = sizeof(R) == 8 ? R(1e-300) : R(1e-37);
-    R p = R(0.5) * (pL + pR) - R(0.125) * du * (rL + rR) * (cL + cR);
+    R p = p0 > R(0) ? p0 : R(0.5) * (pL + pR) - R(0.125) * du * (rL + rR) * (cL + cR);
     if (p < eps) p = eps;
     int it;
     for (it = 1; it <= maxit; ++it) {
@@ -157,6 +161,7 @@ __device__ int exact_star(const R WL[NV], const R WR[NV], R g, R tol, int maxit,
     side_f(p, rR, pR, cR, g, fR, dfR);
     ps = p;
     us = R(0.5) * (uL + uR) + R(0.5) * (fR - fL);
+    if (iters) *iters = it > maxit ? maxit : it;
     return it > maxit ? AMR_ENOCONV : 0;
 }
 

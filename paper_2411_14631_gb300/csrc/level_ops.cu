@@ -158,7 +158,7 @@ static amr_status check(const amr_tree *t, const hydro_params *p)
 {
     if (!t || !p || t->noct <= 0) return AMR_EINVAL;
     if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->rho_floor > 0.0) || !(p->p_floor > 0.0)) return AMR_EINVAL;
-    if (p->riemann < AMR_RIEMANN_HLLC || p->riemann > AMR_RIEMANN_MLP) return AMR_EINVAL;
+    if (p->riemann < AMR_RIEMANN_HLLC || p->riemann > AMR_RIEMANN_MLP_SEEDED) return AMR_EINVAL;
     if (p->precision != AMR_PREC_FP64 && p->precision != AMR_PREC_FP32) return AMR_EINVAL;
     if (p->tile < 0 || p->tile > 2) return AMR_EINVAL;
     return AMR_OK;
@@ -250,7 +250,9 @@ extern "C" amr_status hydro_godunov_level(const amr_tree *t, int level, const hy
                                           amr_stream stream)
 {
     if (check(t, p) != AMR_OK || !d_u_old || !d_u_new || !d_dt) return AMR_EINVAL;
-    if (p->riemann == AMR_RIEMANN_MLP && (p->precision != AMR_PREC_FP32 || !p->mlp_weights)) return AMR_EINVAL;
+    if ((p->riemann == AMR_RIEMANN_MLP || p->riemann == AMR_RIEMANN_MLP_SEEDED) &&
+        (p->precision != AMR_PREC_FP32 || !p->mlp_weights))
+        return AMR_EINVAL;
     if (level != -1 && (level < t->levelmin || level > t->levelmax)) return AMR_EINVAL;
     if (t->levelmax > t->levelmin && !d_flux_reg) return AMR_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

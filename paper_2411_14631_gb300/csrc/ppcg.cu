@@ -256,19 +256,35 @@ struct IterSmem {
     static constexpr int H = PC ? 2 : 1;          // in-plane halo of the w tile
     static constexpr int WX = TX + 2 * H, WY = TY + 2 * H;
     static constexpr int MX = TX + 2, MY = TY + 2;
-    double w[4][WY * WX];
+    static constexpr int RW = 5;                  // w planes in flight or in use
+    double w[RW][WY * WX];
     double m[PC ? 3 : 1][PC ? MY * MX : 1];
     double red[2 * TX * TY / 32];
 };
 
+// 8-byte asynchronous global -> shared copy; zero-filled when !valid (nothing is read)
+__device__ __forceinline__ void cp_async8(double *dst, const double *src, bool valid)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // One PPCG iteration (see the file comment).  Grid: (ceil(nx/32), ceil(ny/TY), ceil(nz/seg)).
+// Step k of a block's z march: the copy of w plane k+3 (k+2 without preconditioner) is
+// started and the seven vectors of cell (x, y, k) are loaded before the block waits for
+// w plane k+2 and computes m plane k+1, so both kinds of memory latency overlap the
+// previous plane's arithmetic.
 template <int TY, bool PC>
 __global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY)) k_iter(Dims d, Vecs v, double *__restrict__ x, PState *st,
                                                                   double *part, double *eps, int seg)
 {
     constexpr int NT = TX * TY;
     using S = IterSmem<TY, PC>;
-    constexpr int H = S::H, WX = S::WX, WY = S::WY, MX = S::MX, MY = S::MY;
+    constexpr int H = S::H, WX = S::WX, WY = S::WY, MX = S::MX, MY = S::MY, RW = S::RW;
+    constexpr int AHEAD = PC ? 3 : 2;             // w plane started at step k: k + AHEAD
     __shared__ S sm;
     if (st->done) return;
     const int it = st->it;
@@ -282,22 +298,21 @@ __global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY)) k_iter(Dims d, Vecs 
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < d.nx && gy < d.ny;
 
-    // w plane k (zero outside the box) with the in-plane halo, into ring slot k & 3
+    // start copying w plane k (zero outside the box) with the in-plane halo into slot k mod RW
     auto load_w = [&](int k) {
-        double *dst = sm.w[k & 3];
+        double *dst = sm.w[(k + RW) % RW];
         const bool zin = k >= 0 && k < d.nz;
         for (int e = tid; e < WX * WY; e += NT) {
             const int ex = e % WX, ey = e / WX;
             const int ix = x0 - H + ex, iy = y0 - H + ey;
-            double val = 0.0;
-            if (zin && ix >= 0 && ix < d.nx && iy >= 0 && iy < d.ny) val = win[ix + d.sy * iy + d.sz * k];
-            dst[e] = val;
+            const bool ok = zin && ix >= 0 && ix < d.nx && iy >= 0 && iy < d.ny;
+            cp_async8(dst + e, ok ? win + (ix + d.sy * iy + d.sz * k) : win, ok);
         }
     };
     // m = 6 M^-1 w on plane k with a one-cell halo (zero outside the box), into slot k mod 3
     auto comp_m = [&](int k) {
         double *dst = sm.m[(k + 3) % 3];
-        const double *wm = sm.w[(k - 1) & 3], *wc = sm.w[k & 3], *wp = sm.w[(k + 1) & 3];
+        const double *wm = sm.w[(k - 1 + RW) % RW], *wc = sm.w[(k + RW) % RW], *wp = sm.w[(k + 1) % RW];
         const bool zin = k >= 0 && k < d.nz;
         for (int e = tid; e < MX * MY; e += NT) {
             const int ex = e % MX, ey = e / MX;
@@ -313,29 +328,39 @@ __global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY)) k_iter(Dims d, Vecs 
     };
 
     double ga = 0.0, da = 0.0;
+    for (int k = z0 - H; k < z0 + AHEAD; k++) load_w(k);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
     if (PC) {
-        for (int k = z0 - 2; k <= z0 + 1; k++) load_w(k);
-        __syncthreads();
         comp_m(z0 - 1);
         comp_m(z0);
         __syncthreads();
-    } else {
-        load_w(z0 - 1);
-        load_w(z0);
     }
     for (int k = z0; k < z1; k++) {
+        load_w(k + AHEAD);
+        cp_async_commit();
+        const int64_t c = gx + d.sy * gy + d.sz * k;
+        double rc = 0.0, xc = 0.0, uc = 0.0, zo = 0.0, so = 0.0, po = 0.0, qo = 0.0;
+        if (own) {
+            rc = v.r[c];
+            xc = x[c];
+            if (PC) uc = v.u[c];
+            if (!first) {
+                zo = v.z[c];
+                so = v.s[c];
+                po = v.p[c];
+                if (PC) qo = v.q[c];
+            }
+        }
+        cp_async_wait<1>();
+        __syncthreads();
         if (PC) {
-            load_w(k + 2);
-            __syncthreads();
             comp_m(k + 1);
-            __syncthreads();
-        } else {
-            load_w(k + 1);
             __syncthreads();
         }
         if (!own) continue;
-        const int64_t c = gx + d.sy * gy + d.sz * k;
-        const double *wk = sm.w[k & 3];
+        const double *wk = sm.w[k % RW];
         const double wc = wk[(ty + H) * WX + tx + H];
         double mc, nval;
         if (PC) {
@@ -347,20 +372,19 @@ __global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY)) k_iter(Dims d, Vecs 
         } else {
             const int wi = (ty + H) * WX + tx + H;
             const double s = ((wk[wi - 1] + wk[wi + 1]) + (wk[wi - WX] + wk[wi + WX])) +
-                             (sm.w[(k + 3) & 3][wi] + sm.w[(k + 1) & 3][wi]);
+                             (sm.w[(k + RW - 1) % RW][wi] + sm.w[(k + 1) % RW][wi]);
             mc = wc;
             nval = fma(6.0, wc, -s);
+            uc = rc;
         }
-        double rc = v.r[c], xc = x[c];
-        double uc = PC ? v.u[c] : rc;
         double zz, ss, pp, qq;
         if (first) {
             zz = nval; ss = wc; pp = uc; qq = mc;
         } else {
-            zz = fma(beta, v.z[c], nval);
-            ss = fma(beta, v.s[c], wc);
-            pp = fma(beta, v.p[c], uc);
-            qq = PC ? fma(beta, v.q[c], mc) : ss;
+            zz = fma(beta, zo, nval);
+            ss = fma(beta, so, wc);
+            pp = fma(beta, po, uc);
+            qq = PC ? fma(beta, qo, mc) : ss;
         }
         xc = fma(alpha, pp, xc);
         rc = fma(-alpha, ss, rc);
@@ -376,6 +400,7 @@ __global__ void __launch_bounds__(TX *TY, 1024 / (TX * TY)) k_iter(Dims d, Vecs 
         ga = fma(rc, uc, ga);
         da = fma(wn, uc, da);
     }
+    cp_async_wait<0>();
     const int nb = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (grid_sum2<NT>(ga, da, sm.red, part, st, nb, bid)) {
@@ -412,7 +437,7 @@ struct Launch {
 
 amr_status plan(const ppcg_params *prm, Launch &L)
 {
-    L.ty = prm->tile_y ? prm->tile_y : 16;
+    L.ty = prm->tile_y ? prm->tile_y : 8;
     if (L.ty != 8 && L.ty != 16) return AMR_EINVAL;
     const int cx = (prm->nx + TX - 1) / TX, cy = (prm->ny + L.ty - 1) / L.ty;
     int seg = prm->seg;

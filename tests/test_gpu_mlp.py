@@ -164,8 +164,9 @@ def test_godunov_with_surrogate(oracle, H):
     w0 = W.sod_prims(cell_centres_of(tree))
     res = {}
     for name, riemann, tol in (("exact", abi.RIEMANN_EXACT, 0.0), ("mlp_tol0", abi.RIEMANN_MLP, 0.0),
-                               ("mlp", abi.RIEMANN_MLP, 0.05), ("hllc", abi.RIEMANN_HLLC, 0.0)):
-        prm = H.Params(1.4, cfl=0.8, riemann=riemann, precision=abi.PREC_FP32)
+                               ("mlp", abi.RIEMANN_MLP, 0.05), ("hllc", abi.RIEMANN_HLLC, 0.0),
+                               ("exact_tiles", abi.RIEMANN_EXACT, 0.0), ("seeded", abi.RIEMANN_MLP_SEEDED, 0.0)):
+        prm = H.Params(1.4, cfl=0.8, riemann=riemann, precision=abi.PREC_FP32, tiles_only=name == "exact_tiles")
         prm.c.mlp_weights = sur.packed.data_ptr()
         prm.c.mlp_resid_tol = tol
         sim = H.Simulation(tree, prm, w0=w0)
@@ -184,3 +185,16 @@ def test_godunov_with_surrogate(oracle, H):
     l1_mlp = np.abs(um[0] - ue[0]).sum() / np.abs(ue[0]).sum()
     l1_hllc = np.abs(uh[0] - ue[0]).sum() / np.abs(ue[0]).sum()
     assert l1_mlp < 1e-3, (l1_mlp, l1_hllc)
+    # seeded Newton: every face gets the exact solver's answer to its tolerance.  The
+    # network's guess lies inside Newton's fast basin (a few iterations); on the Sod tube
+    # most faces separate equal states, where the linearised guess is already exact, so
+    # the cold start needs about one iteration and the seeded one about two.
+    st2, cnt2 = res["seeded"][1]
+    ste, cnte = res["exact_tiles"][1]
+    assert st2 == 0 and ste == 0
+    assert cnt2[3] == cnt2[0] + cnt2[1] and cnt2[0] > 0.9 * cnt2[3], cnt2
+    assert cnte[3] == cnt2[3]
+    it_seeded, it_cold = cnt2[2] / cnt2[3], cnte[2] / cnte[3]
+    assert it_seeded <= 3.0 and it_cold <= 3.0, (it_seeded, it_cold)
+    l1_seeded = np.abs(res["seeded"][0][0] - ue[0]).sum() / np.abs(ue[0]).sum()
+    assert l1_seeded < 2e-5 and l1_seeded < 0.1 * l1_hllc, (l1_seeded, l1_hllc)

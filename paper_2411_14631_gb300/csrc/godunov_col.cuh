@@ -41,7 +41,7 @@ struct ColArgs {
     int32_t finer;          // the level has refined cells (finer levels exist)
     int level;
     int64_t n;              // cells per dimension
-    int zc;                 // segment length in cells (multiple of 2, divides n)
+    int zc;                 // segment length in cells (power of two, divides n)
     const double *u_old;
     double *u_new;
     const double *dt;
@@ -155,45 +155,46 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         const R lamR = to_work<R>(lam);
         const R hl = R(0.5) * lamR;
         const R dxR = to_work<R>(dx);
+        // cell coordinates, oct and cell ids fit in 32 bits (at most 2^12 cells per axis and
+        // fewer than 2^27 octs)
+        const int ni = int(n);
         const int64_t nfx = n / FX, nfy = n / FY;
         const int64_t fxy = wb % (nfx * nfy), seg = wb / (nfx * nfy);
-        const int64_t X0 = (fxy % nfx) * FX - 2, Y0 = (fxy / nfx) * FY - 2;   // stencil index 0
-        const int64_t z0 = seg * a.zc;
-        auto wrap = [&](int64_t c, int axis) -> int64_t {
-            if (c >= 0 && c < n) return c;
-            if (per[axis]) return (c + n) % n;
-            return c < 0 ? 0 : n - 1;              // outflow: clamp at this level
+        const int X0 = int(fxy % nfx) * FX - 2, Y0 = int(fxy / nfx) * FY - 2;   // stencil index 0
+        const int z0 = int(seg) * a.zc;
+        auto wrap = [&](int c, int axis) -> int {
+            if (c >= 0 && c < ni) return c;
+            if (per[axis]) return c < 0 ? c + ni : c - ni;   // within one period of the box
+            return c < 0 ? 0 : ni - 1;             // outflow: clamp at this level
         };
-        // oct and cell ids fit in 32 bits (fewer than 2^27 octs)
         const int32_t Mi = int32_t(M);
-        auto cell_id = [&](int64_t X, int64_t Y, int64_t Z) -> int32_t {
-            const int32_t x = int32_t(X), y = int32_t(Y), z = int32_t(Z);
+        auto cell_id = [&](int x, int y, int z) -> int32_t {
             const int32_t oi = (x >> 1) + Mi * ((y >> 1) + Mi * (z >> 1));
             const int32_t o = batch ? obase + oi : a.grid[oi];
             return o * 8 + (x & 1) + 2 * (y & 1) + 4 * (z & 1);
         };
 
         // gather oct layer L (cell planes 2L, 2L+1) of the stencil footprint into the W ring
-        auto gather = [&](int64_t L) {
+        auto gather = [&](int L) {
             for (int q = tid; q < (SX / 2) * (SY / 2) * 8; q += nt) {
                 const int o = q >> 3, c = q & 7;
                 const int i = 2 * (o % (SX / 2)) + (c & 1), j = 2 * (o / (SX / 2)) + ((c >> 1) & 1);
-                const int64_t zp = 2 * L + ((c >> 2) & 1);
+                const int zp = 2 * L + ((c >> 2) & 1);
                 const int32_t cid = cell_id(wrap(X0 + i, 0), wrap(Y0 + j, 1), wrap(zp, 2));
                 R Uw[NV], Wc[NV];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(uo[v][cid]);
                 cons_to_prim_w(Uw, pr, Wc);
-                const int slot = int(zp & 3);
+                const int slot = zp & 3;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) sm.W[slot][v][i + SX * j] = Wc[v];
-                if constexpr (FINER) sm.ref[int(zp & 7)][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
+                if constexpr (FINER) sm.ref[zp & 7][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
             }
         };
-        auto q3 = [](int64_t p) { return int((p + 6) % 3); };   // planes start at z0 - 2 >= -2
+        auto q3 = [](int p) { return (p + 6) % 3; };   // planes start at z0 - 2 >= -2
         // MinMod slopes + MUSCL-Hancock predictor of plane p (cells 1..SX-2 x 1..SY-2)
-        auto predict = [&](int64_t p) {
-            const int s0 = int(p & 3), sm1 = int((p - 1) & 3), sp1 = int((p + 1) & 3), qs = q3(p);
+        auto predict = [&](int p) {
+            const int s0 = p & 3, sm1 = (p - 1) & 3, sp1 = (p + 1) & 3, qs = q3(p);
             for (int r = tid; r < PX * PY; r += nt) {
                 const int i = 1 + r % PX, j = 1 + r / PX;
                 const int si = i + SX * j;
@@ -223,28 +224,30 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             }
         };
         // z faces below planes j (face j-1 | j), for the listed planes
-        auto zfaces = [&](int64_t j0, int count) {
+        auto zfaces = [&](int j0, int count) {
+            const int qa = q3(j0 - 1), qb = q3(j0), qc = q3(j0 + 1);
             for (int r = tid; r < count * FX * FY; r += nt) {
-                const int64_t j = j0 + r / (FX * FY);
+                const int dj = r / (FX * FY);          // FX * FY is a power of two
                 const int rr = r % (FX * FY), x = rr % FX, y = rr / FX;
                 const int pq = (1 + x) + PX * (1 + y);
                 R WL[NV], WR[NV], Fn[NV];
-                col_face<R, 2, PX * PY>(sm.Q[q3(j - 1)], sm.Q[q3(j)], pq, pq, pr, WL, WR);
+                col_face<R, 2, PX * PY>(sm.Q[dj ? qb : qa], sm.Q[dj ? qc : qb], pq, pq, pr, WL, WR);
                 col_solve<R, RS>(WL, WR, pr, a.status, Fn);
-                col_store<2>(sm.Fz[q3(j)], rr, Fn);
+                col_store<2>(sm.Fz[dj ? qc : qb], rr, Fn);
             }
         };
 
         constexpr int NXF = FY * (FX + 1), NYF = (FY + 1) * FX;
         constexpr int NG = (SX / 2) * (SY / 2) * 8, NU = 2 * FX * FY, NR = (FX / 2) * (FY / 2) * NV;
         // x and y faces of planes k, k+1 and z faces below planes k+1, k+2 (those of slab k)
-        auto slab_faces = [&](int64_t k) {
+        auto slab_faces = [&](int k) {
+            const int qk0 = q3(k), qk1 = q3(k + 1);
             for (int r = tid; r < 2 * (NXF + NYF); r += nt) {
                 R WL[NV], WR[NV], Fn[NV];
                 if (r < 2 * NXF) {
                     const int dz = r / NXF, rr = r % NXF, fa = rr % (FX + 1), row = rr / (FX + 1);
                     const int pl = fa + PX * (1 + row);
-                    const int qs = q3(k + dz);
+                    const int qs = dz ? qk1 : qk0;
                     col_face<R, 0, PX * PY>(sm.Q[qs], sm.Q[qs], pl, pl + 1, pr, WL, WR);
                     col_solve<R, RS>(WL, WR, pr, a.status, Fn);
                     col_store<0>(sm.Fx[dz], rr, Fn);
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                     const int r2 = r - 2 * NXF;
                     const int dz = r2 / NYF, rr = r2 % NYF, col = rr % FX, fa = rr / FX;
                     const int pl = (1 + col) + PX * fa;
-                    const int qs = q3(k + dz);
+                    const int qs = dz ? qk1 : qk0;
                     col_face<R, 1, PX * PY>(sm.Q[qs], sm.Q[qs], pl, pl + PX, pr, WL, WR);
                     col_solve<R, RS>(WL, WR, pr, a.status, Fn);
                     col_store<1>(sm.Fy[dz], rr, Fn);
@@ -261,29 +264,30 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             zfaces(k + 1, 2);
         };
         // FP64 update of cell q of slab k (fused CFL candidate); keeps the new state
-        auto update = [&](int64_t k, int q) {
+        auto update = [&](int k, int q) {
             const int dz = q / (FX * FY), r = q % (FX * FY), x = r % FX, y = r / FX;
-            const int64_t p = k + dz;
-            const int ub = int((k >> 1) & 1);
+            const int p = k + dz;
+            const int ub = (k >> 1) & 1;
             // with finer levels: a refined cell is left to the restriction, and a face whose
             // other side is refined carries no flux here (the finer level supplies it)
             bool sk[6] = {false, false, false, false, false, false};
             if constexpr (FINER) {
                 const int si = (x + 2) + SX * (y + 2);
-                const uint8_t *rp = sm.ref[int(p & 7)];
+                const uint8_t *rp = sm.ref[p & 7];
                 if (rp[si]) { sm.cell[ub][q] = -1; return; }
                 sk[0] = rp[si - 1]; sk[1] = rp[si + 1]; sk[2] = rp[si - SX]; sk[3] = rp[si + SX];
-                sk[4] = sm.ref[int((p - 1) & 7)][si]; sk[5] = sm.ref[int((p + 1) & 7)][si];
+                sk[4] = sm.ref[(p - 1) & 7][si]; sk[5] = sm.ref[(p + 1) & 7][si];
             }
             R dU[NV] = {0, 0, 0, 0, 0};
+            const int fzl = q3(p), fzu = fzl == 2 ? 0 : fzl + 1;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 if (!sk[0]) dU[v] = dU[v] + sm.Fx[dz][v][x + (FX + 1) * y];
                 if (!sk[1]) dU[v] = dU[v] - sm.Fx[dz][v][x + 1 + (FX + 1) * y];
                 if (!sk[2]) dU[v] = dU[v] + sm.Fy[dz][v][x + FX * y];
                 if (!sk[3]) dU[v] = dU[v] - sm.Fy[dz][v][x + FX * (y + 1)];
-                if (!sk[4]) dU[v] = dU[v] + sm.Fz[q3(p)][v][r];
-                if (!sk[5]) dU[v] = dU[v] - sm.Fz[q3(p + 1)][v][r];
+                if (!sk[4]) dU[v] = dU[v] + sm.Fz[fzl][v][r];
+                if (!sk[5]) dU[v] = dU[v] - sm.Fz[fzu][v][r];
             }
             const bool nbref = sk[0] || sk[1] || sk[2] || sk[3] || sk[4] || sk[5];
             const int32_t cid = cell_id(X0 + 2 + x, Y0 + 2 + y, p);
@@ -299,9 +303,9 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             if (dtn && !nbref) my_dt = min(my_dt, (unsigned long long)__double_as_longlong(cfl_candidate<R>(Un, pr, cflR, dxR)));
         };
         // restriction of the father of one oct of slab k (its eight cells in order), variable v
-        auto restrict_one = [&](int64_t k, int w) {
+        auto restrict_one = [&](int k, int w) {
             const int o = w / NV, v = w % NV, oi = o % (FX / 2), oj = o / (FX / 2);
-            const int ub = int((k >> 1) & 1);
+            const int ub = (k >> 1) & 1;
             const int q0 = 2 * oi + FX * (2 * oj);
             const int32_t c0 = sm.cell[ub][q0];
             if (c0 < 0) return;                       // a refined cell: the oct is not restricted here
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         __syncthreads();
         // per slab k: {update of slab k, gather of the layer slab k+2 needs, restriction of
         // slab k-2} share one phase, then the predictions and faces of slab k+2
-        for (int64_t k = z0; k < z0 + a.zc; k += 2) {
+        for (int k = z0; k < z0 + a.zc; k += 2) {
             const bool more = k + 2 < z0 + a.zc;
             const int nwork = NU + (more ? NG : 0) + (k > z0 ? NR : 0);
             for (int w = tid; w < nwork; w += nt) {
@@ -342,15 +346,15 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 } else if (more && w < NU + NG) {
                     const int q = w - NU, o = q >> 3, c = q & 7;
                     const int i = 2 * (o % (SX / 2)) + (c & 1), j = 2 * (o / (SX / 2)) + ((c >> 1) & 1);
-                    const int64_t zp = k + 4 + ((c >> 2) & 1);
+                    const int zp = k + 4 + ((c >> 2) & 1);
                     const int32_t cid = cell_id(wrap(X0 + i, 0), wrap(Y0 + j, 1), wrap(zp, 2));
                     R Uw[NV], Wc[NV];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(uo[v][cid]);
                     cons_to_prim_w(Uw, pr, Wc);
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) sm.W[int(zp & 3)][v][i + SX * j] = Wc[v];
-                    if constexpr (FINER) sm.ref[int(zp & 7)][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
+                    for (int v = 0; v < NV; ++v) sm.W[zp & 3][v][i + SX * j] = Wc[v];
+                    if constexpr (FINER) sm.ref[zp & 7][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
                 } else {
                     if (!batch) restrict_one(k - 2, w - NU - (more ? NG : 0));
                 }
@@ -400,7 +404,12 @@ amr_status launch_col(const amr_tree *t, const hydro_params *p, const double *u_
     } else {
         a.level = t->grid_level;
         a.n = int64_t(1) << t->grid_level;
-        a.zc = a.n < 32 ? int(a.n) : 32;
+        // longest segment (at most 64 cells, fewer prologue planes per cell) that still
+        // gives two waves of four CTAs per SM
+        int dev = 0, nsm = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        a.zc = a.n < 64 ? int(a.n) : 64;
+        while (a.zc > 16 && (a.n / FX) * (a.n / FY) * (a.n / a.zc) < int64_t(8) * nsm) a.zc /= 2;
         a.work = (a.n / FX) * (a.n / FY) * (a.n / a.zc);
     }
     a.u_old = u_old; a.u_new = u_new; a.dt = dt; a.dt_next = dt_next;

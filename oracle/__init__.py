@@ -18,7 +18,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = ["riemann.c", "tree.c", "hydro.c", "mlp.c", "box.c", "poisson.c"]
+_SRC = ["riemann.c", "tree.c", "hydro.c", "mlp.c", "box.c", "poisson.c", "refine.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 OK, EINVAL, EUNBALANCED, ENONPHYSICAL, ENOCONV, EBREAKDOWN = 0, -1, -2, -6, -7, -8
@@ -88,6 +88,9 @@ def lib():
         L.or_adam_step.argtypes = [P, P, P, P, C.c_int64, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_int64]
         I = C.c_int
+        L.or_refine_flags.argtypes = [P, P, C.c_double, I, P]
+        L.or_refine_list.argtypes = [P, P, C.c_double, I, P, C.c_int64, C.POINTER(C.c_int64)]
+        L.or_remap.argtypes = [P, P, P, P]
         L.or_poisson_apply_A.argtypes = [I, I, I, P, P]
         L.or_poisson_apply_Minv.argtypes = [I, I, I, I, P, P]
         for f in (L.or_cg, L.or_ppcg):
@@ -199,6 +202,29 @@ class Tree:
     def reflux_restrict(self, level, reg, u_new, dt, prm):
         return lib().or_reflux_restrict(self._h, C.byref(prm), level, _p(reg) if reg is not None else None,
                                         _p(u_new), dt)
+
+    # ---- refinement (refine_fine) ----------------------------------------------------
+    def refine_flags(self, u, mass_thr, lmax):
+        u = _f64(u)
+        f = np.zeros(self.ncell, np.uint8)
+        st = lib().or_refine_flags(self._h, _p(u), mass_thr, lmax, _p(f))
+        return f, st
+
+    def refine_list(self, u, mass_thr, lmax):
+        """New oct list (level, ix, iy, iz) after refinement by mass (refine.c)."""
+        u = _f64(u)
+        cap = self.ncell + 1
+        out = np.zeros((cap, 4), np.int32)
+        n = C.c_int64()
+        st = lib().or_refine_list(self._h, _p(u), mass_thr, lmax, _p(out), cap, C.byref(n))
+        return out[:n.value].copy(), st
+
+    def remap(self, u, new_tree):
+        """State on new_tree: copied where the cell exists here, interpolated otherwise."""
+        u = _f64(u)
+        un = np.empty((5, new_tree.ncell))
+        st = lib().or_remap(self._h, _p(u), new_tree._h, _p(un))
+        return un, st
 
     def stencil(self, u, oct_id):
         u = _f64(u)

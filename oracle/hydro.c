@@ -392,3 +392,10 @@ int or_prim_of_state(const or_tree *t, const or_params *p, const double *u, doub
     }
     return OR_OK;
 }
+
+/* the value of level-l cell (X,Y,Z): its own state, or the interpolation from its father
+   used for ghost cells when it does not exist (returns -1 then, < -1 if unbalanced) */
+int64_t or_cell_value(const or_tree *t, const double *u, int l, int64_t X, int64_t Y, int64_t Z, double *U)
+{
+    return cell_value(t, u, l, X, Y, Z, U);
+}

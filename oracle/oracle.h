@@ -97,6 +97,13 @@ void or_mlp_backward(const double *theta, const double *x, const double *dy, int
 void or_adam_step(double *th, double *m, double *v, const double *grad, int64_t n, double lr,
                   double beta1, double beta2, double eps, int64_t t);
 
+/* refinement between steps (refine.c) */
+int or_refine_flags(const or_tree *t, const double *u, double mass_thr, int lmax, uint8_t *flag /*[8 noct]*/);
+int or_refine_list(const or_tree *t, const double *u, double mass_thr, int lmax, int32_t *lxyz /*[cap][4]*/,
+                   int64_t cap, int64_t *n_out);
+int or_remap(const or_tree *t_old, const double *u_old, const or_tree *t_new, double *u_new);
+int64_t or_cell_value(const or_tree *t, const double *u, int l, int64_t X, int64_t Y, int64_t Z, double *U);
+
 /* Poisson solve on a box of nx*ny*nz cells, vectors indexed i + nx (j + ny k) (poisson.c) */
 enum { OR_PRECOND_NONE = 0, OR_PRECOND_IP = 1 };
 void or_poisson_apply_A(int nx, int ny, int nz, const double *x, double *y);

@@ -558,6 +558,24 @@ def study_amr(args):
         scale = np.array([max(np.sum(np.abs(u0[v, leaf]) * vol), np.sum(np.abs(u1[v, leaf]) * vol))
                           for v in range(5)])
         out["conservation_" + name] = {"steps": 10, "rel_drift": [float(x) for x in np.abs(tot1 - tot0) / scale]}
+        if prec == abi.PREC_FP32:
+            # refine_fine on the evolved state: flags, 2:1 balance, device oct list, the new
+            # tree (Hilbert keys, sort, tables) and the state remap
+            thr = 2.0 ** -21
+            tree.refine(sim.u, thr, 12)                 # warm-up (allocations, first launches)
+            torch.cuda.synchronize()
+            t0r = time.perf_counter()
+            reps = 5
+            for _ in range(reps):
+                new, u_new = tree.refine(sim.u, thr, 12)
+            torch.cuda.synchronize()
+            dtr = (time.perf_counter() - t0r) / reps
+            out["refine"] = {"ms": dtr * 1e3, "octs_before": tree.noct, "octs_after": new.noct,
+                             "levelmax_after": new.levelmax, "mass_thr": thr,
+                             "note": "wall time of Octree.refine (three synchronising C calls, buffers allocated "
+                                     "by the caller each time), after 10 FP32 steps",
+                             "step_ms_fp32": res["fp32_chosen"]["ms_per_step"]}
+            del new, u_new
     print(json.dumps(out))
     return 0
 

@@ -272,6 +272,57 @@ amr_status hydro_harvest_faces(const amr_tree *tree, const hydro_params *params,
                                const double *d_dt, double *d_states, int64_t capacity, int64_t stride,
                                unsigned long long *d_count, amr_stream stream);
 
+/* ---- refinement between steps (refine_fine, Table 1) ------------------------------
+   The paper names the routine, not its rules.  The rules here:
+     - a cell at level l, levelmin <= l < params->levelmax, is refined iff its mass
+       rho dx_l^3 exceeds params->mass_thr (rho is the cell's own density; a refined cell
+       holds the mean of its children); cells above levelmin always are (levels
+       1..levelmin stay complete), cells at params->levelmax or deeper never are;
+     - 2:1 balance, level by level from the finest up: a refined cell also refines the
+       parent-level cells containing its 26 neighbours (2 per axis); nothing is needed
+       beyond an outflow face, periodic faces wrap;
+     - a cell exists iff its father is refined: the new oct list is the root oct plus the
+       child oct of every refined cell (octs whose father is no longer refined are
+       dropped, several levels at once if needed; new octs appear one level at a time).
+   The three calls: amr_refine (the new oct list, on the device), amr_build_octree_device
+   (the new tree from it) and amr_remap_state (the state on the new tree). */
+typedef struct {
+    double mass_thr;      /* refine a cell iff rho dx^3 > mass_thr (>= 0) */
+    int32_t levelmax;     /* deepest level the new tree may have, levelmin .. 20 */
+    int32_t pad;
+} amr_refine_params;
+
+/* Scratch bytes amr_refine needs for tree t (0 for a batch tree). */
+size_t amr_refine_work_bytes(const amr_tree *t);
+
+/* The refined tree's oct list from state d_u (conserved FP64 SoA of t): d_lxyz receives
+   (level, ix, iy, iz) for *h_n octs in no particular order (cap >= 8 * t->noct + 1
+   entries of 4 int32); h_level_counts[0 .. AMR_MAXLEV] the octs per level.  d_work:
+   amr_refine_work_bytes(t) bytes, 256-byte aligned.  Synchronises.  AMR_EINVAL for bad
+   arguments, AMR_ECAPACITY for short buffers, AMR_EUNBALANCED if t breaks the 2:1 rule. */
+amr_status amr_refine(const amr_tree *t, const amr_refine_params *params, const double *d_u, void *d_work,
+                      size_t work_bytes, int32_t *d_lxyz, int64_t cap, int64_t *h_level_counts, int64_t *h_n,
+                      amr_stream stream);
+
+/* amr_build_octree for an oct list already on the device, with its octs per level
+   h_level_counts[0 .. AMR_MAXLEV] (checked against the list; AMR_EINVAL if they differ).
+   Octree mode only (geom->n_inst == 0).  Synchronises. */
+amr_status amr_build_octree_device_query(const amr_geom *geom, const int64_t *h_level_counts, size_t *tree_bytes,
+                                         size_t *workspace_bytes);
+amr_status amr_build_octree_device(const amr_geom *geom, const int32_t *d_oct_lxyz, const int64_t *h_level_counts,
+                                   void *d_tree_mem, size_t tree_bytes, void *d_workspace, size_t workspace_bytes,
+                                   amr_tree *out, amr_stream stream);
+
+/* The state on t_new from the state on t_old (both FP64 SoA, distinct buffers): an oct
+   present in both trees is copied; a new oct's cells are interpolated from their father
+   cell in t_old with the ghost-cell formula
+     U = U_F + sum_d s_d/4 minmod(U_F - U_{F-e_d}, U_{F+e_d} - U_F),
+   which keeps the leaf totals of mass, momentum and energy.  t_new must come from
+   amr_refine on t_old.  Asynchronous; a father missing from t_old writes
+   AMR_EUNBALANCED to d_status (may be NULL). */
+amr_status amr_remap_state(const amr_tree *t_old, const double *d_u_old, const amr_tree *t_new, double *d_u_new,
+                           int32_t *d_status, amr_stream stream);
+
 /* Copy params->d_status and params->d_counters to the host (synchronises the device). */
 amr_status amr_get_status(const hydro_params *params, int32_t *h_status, unsigned long long *h_counters);
 

@@ -22,7 +22,9 @@ EXPORTS = ["amr_build_octree_query", "amr_build_octree", "hydro_init_from_prim",
            "amr_get_status", "amr_status_string", "hydro_step_static_scratch", "hydro_harvest_faces",
            "mlp_nparams", "mlp_packed_bytes", "mlp_scratch_bytes", "mlp_pack", "mlp_make_dataset", "mlp_forward",
            "mlp_grad", "mlp_train_step",
-           "ppcg_workspace_bytes", "poisson_apply", "ppcg_start", "ppcg_iterate", "ppcg_poll", "ppcg_solve"]
+           "ppcg_workspace_bytes", "poisson_apply", "ppcg_start", "ppcg_iterate", "ppcg_poll", "ppcg_solve",
+           "amr_refine_work_bytes", "amr_refine", "amr_build_octree_device_query", "amr_build_octree_device",
+           "amr_remap_state"]
 MLP_NPARAMS = 8962
 STATIC_REG_MAX_OCTS = 131072
 
@@ -49,6 +51,10 @@ class AmrTree(C.Structure):
                 ("tile_slot", C.c_void_p * 2), ("n_inst", C.c_int32), ("inst_n", C.c_void_p), ("inst_dx", C.c_void_p),
                 ("inst_oct_off", C.c_void_p), ("tile_inst", C.c_void_p * 2), ("grid_level", C.c_int32),
                 ("grid", C.c_void_p), ("col_work", C.c_int64), ("inst_col_off", C.c_void_p)]
+
+
+class RefineParams(C.Structure):
+    _fields_ = [("mass_thr", C.c_double), ("levelmax", C.c_int32), ("pad", C.c_int32)]
 
 
 class PpcgParams(C.Structure):
@@ -98,6 +104,12 @@ def lib():
     L.mlp_forward.argtypes = [P, P, P, C.c_int64, P]
     L.mlp_grad.argtypes = [P, P, P, C.c_int64, P, P, S, P]
     L.mlp_train_step.argtypes = [P, P, P, P, P, P, C.c_int64, C.c_float, C.c_int64, P, P, S, P]
+    L.amr_refine_work_bytes.argtypes = [PT]
+    L.amr_refine_work_bytes.restype = S
+    L.amr_refine.argtypes = [PT, C.POINTER(RefineParams), P, P, S, P, C.c_int64, P, C.POINTER(C.c_int64), P]
+    L.amr_build_octree_device_query.argtypes = [C.POINTER(AmrGeom), P, C.POINTER(S), C.POINTER(S)]
+    L.amr_build_octree_device.argtypes = [C.POINTER(AmrGeom), P, P, P, S, P, S, PT, P]
+    L.amr_remap_state.argtypes = [PT, P, PT, P, P, P]
     PG = C.POINTER(PpcgParams)
     I = C.c_int32
     L.ppcg_workspace_bytes.argtypes = [I, I, I]
@@ -112,7 +124,7 @@ def lib():
     L.amr_status_string.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("hydro_flux_reg_bytes", "amr_status_string", "mlp_packed_bytes", "mlp_scratch_bytes",
-                        "ppcg_workspace_bytes"):
+                        "ppcg_workspace_bytes", "amr_refine_work_bytes"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L

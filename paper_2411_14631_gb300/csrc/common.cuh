@@ -112,6 +112,8 @@ struct TreeView {
     const int32_t *lvl, *ix, *iy, *iz;
     const int32_t *son, *nbor, *father;
     const uint8_t *refmask, *fused;
+    const uint64_t *key;                 // Hilbert keys (octs sorted by level, then key)
+    const int32_t *nb27;                 // same-level neighbour octs (refinement)
     int32_t n_inst;                      // batch mode: number of boxes (0: octree)
     const int32_t *inst_n;
     const double *inst_dx;
@@ -129,6 +131,7 @@ inline TreeView make_view(const amr_tree *t)
     v.reg_base = t->reg_base;
     v.lvl = t->lvl; v.ix = t->ix; v.iy = t->iy; v.iz = t->iz;
     v.son = t->son; v.nbor = t->nbor; v.father = t->father; v.refmask = t->refmask; v.fused = t->fused;
+    v.key = t->key; v.nb27 = t->nb27;
     v.n_inst = t->n_inst; v.inst_n = t->inst_n; v.inst_dx = t->inst_dx;
     return v;
 }

@@ -66,7 +66,7 @@ static WsLayout ws_layout(int64_t n)
     size_t o = 0;
     auto put = [&](size_t bytes) { size_t at = o; o += al256(bytes); return at; };
     W.lxyz = put(16 * n); W.sk0 = put(8 * n); W.sk1 = put(8 * n); W.id0 = put(4 * n); W.id1 = put(4 * n);
-    W.flag = put(4 * (n + 1)); W.pos = put(4 * (n + 1)); W.small = put(1024);
+    W.flag = put(4 * (n + 1)); W.pos = put(4 * (n + 1)); W.small = put(2048);   // err, tile counts, level histogram
     W.cub_bytes = cub_bytes_needed(n);
     W.cub = put(W.cub_bytes);
     W.total = o;
@@ -104,14 +104,23 @@ __global__ void k_keys(const int32_t *__restrict__ lxyz, int64_t n, uint64_t *sk
     if (i >= n) return;
     const int l = lxyz[4 * i];
     const int32_t x = lxyz[4 * i + 1], y = lxyz[4 * i + 2], z = lxyz[4 * i + 3];
-    const int64_t m = int64_t(1) << (l - 1);
-    if (x < 0 || y < 0 || z < 0 || x >= m || y >= m || z >= m) {
+    const int64_t m = int64_t(1) << ((l >= 1 && l <= LMAX_BUILD ? l : 1) - 1);
+    if (l < 1 || l > LMAX_BUILD || x < 0 || y < 0 || z < 0 || x >= m || y >= m || z >= m) {
         set_error(err, AMR_EINVAL);
         sk[i] = ~uint64_t(0);
     } else {
         sk[i] = (uint64_t(l) << 58) | hilbert3(l - 1, x, y, z);
     }
     id[i] = int32_t(i);
+}
+
+// octs per level of a device oct list (checked against the counts the caller gave)
+__global__ void k_level_hist(const int32_t *__restrict__ lxyz, int64_t n, unsigned long long *hist)
+{
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const int l = lxyz[4 * i];
+    if (l >= 0 && l < AMR_MAXLEV + 2) atomicAdd(hist + l, 1ull);
 }
 
 __global__ void k_scatter(const uint64_t *__restrict__ sk, const int32_t *__restrict__ id,
@@ -483,25 +492,12 @@ extern "C" amr_status amr_build_octree_query(const amr_geom *geom, const int32_t
     return AMR_OK;
 }
 
-extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oct_lxyz, int64_t n,
-                                       void *d_tree_mem, size_t tree_bytes, void *d_workspace,
-                                       size_t workspace_bytes, amr_tree *out, amr_stream stream)
+// The octree from an oct list in host memory (h_lxyz) or device memory (d_lxyz), with its
+// per-level counts already known.
+static amr_status build_tree(const amr_geom *geom, const int32_t *h_lxyz, const int32_t *d_lxyz, int64_t n,
+                             const int64_t cnt[AMR_MAXLEV + 2], int lmax, void *d_tree_mem, size_t tree_bytes,
+                             void *d_workspace, size_t workspace_bytes, amr_tree *out, cudaStream_t st)
 {
-    if (geom && geom->n_inst > 0) {
-        if (!d_tree_mem || !d_workspace || !out) return AMR_EINVAL;
-        for (int f = 0; f < 6; ++f)
-            if (geom->bc[f] != AMR_BC_PERIODIC && geom->bc[f] != AMR_BC_OUTFLOW) return AMR_EINVAL;
-        for (int a = 0; a < 3; ++a)
-            if ((geom->bc[2 * a] == AMR_BC_PERIODIC) != (geom->bc[2 * a + 1] == AMR_BC_PERIODIC)) return AMR_EINVAL;
-        if ((uintptr_t(d_tree_mem) & 255) || (uintptr_t(d_workspace) & 255)) return AMR_EINVAL;
-        return build_boxes(geom, d_tree_mem, tree_bytes, d_workspace, workspace_bytes, out,
-                           reinterpret_cast<cudaStream_t>(stream));
-    }
-    if (check_geom(geom, n) != AMR_OK || !h_oct_lxyz || !d_tree_mem || !d_workspace || !out) return AMR_EINVAL;
-    if ((uintptr_t(d_tree_mem) & 255) || (uintptr_t(d_workspace) & 255)) return AMR_EINVAL;
-    int64_t cnt[AMR_MAXLEV + 2];
-    int lmax;
-    if (count_levels(h_oct_lxyz, n, cnt, &lmax) != AMR_OK) return AMR_EINVAL;
     const int lmin = geom->levelmin;
     if (lmax < lmin) return AMR_EINVAL;
     for (int l = 1; l <= lmin; ++l)
@@ -509,7 +505,6 @@ extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oc
     const TreeLayout L = tree_layout(n, cnt, lmin, lmax);
     const WsLayout W = ws_layout(n);
     if (tree_bytes < L.total || workspace_bytes < W.total) return AMR_ECAPACITY;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char *T = static_cast<char *>(d_tree_mem), *S = static_cast<char *>(d_workspace);
 
     std::memset(out, 0, sizeof(*out));
@@ -530,7 +525,7 @@ extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oc
         out->tile_root[d] = (int32_t *)(T + L.root[d]);
         out->tile_slot[d] = (int32_t *)(T + L.slot[d]);
     }
-    int32_t *lxyz = (int32_t *)(S + W.lxyz);
+    const int32_t *lxyz = d_lxyz ? d_lxyz : (const int32_t *)(S + W.lxyz);
     uint64_t *sk0 = (uint64_t *)(S + W.sk0), *sk1 = (uint64_t *)(S + W.sk1);
     int32_t *id0 = (int32_t *)(S + W.id0), *id1 = (int32_t *)(S + W.id1);
     int32_t *flag = (int32_t *)(S + W.flag), *pos = (int32_t *)(S + W.pos);
@@ -538,10 +533,22 @@ extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oc
     int64_t *tcnt = (int64_t *)(S + W.small + 256);
     void *cubtmp = S + W.cub;
 
-    AMR_CUDA_TRY(cudaMemcpyAsync(lxyz, h_oct_lxyz, 16 * size_t(n), cudaMemcpyHostToDevice, st));
-    AMR_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
     const int TB = 256;
     const unsigned nb = unsigned((n + TB - 1) / TB), nb1 = unsigned((n + TB) / TB);
+    if (h_lxyz)
+        AMR_CUDA_TRY(cudaMemcpyAsync(S + W.lxyz, h_lxyz, 16 * size_t(n), cudaMemcpyHostToDevice, st));
+    AMR_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+    if (d_lxyz) {
+        // the caller's per-level counts must describe the list (they size the layout)
+        unsigned long long *hist = (unsigned long long *)(S + W.small + 1024);
+        unsigned long long hh[AMR_MAXLEV + 2];
+        AMR_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(hh), st));
+        k_level_hist<<<nb, TB, 0, st>>>(lxyz, n, hist);
+        AMR_CUDA_TRY(cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, st));
+        AMR_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int l = 0; l < AMR_MAXLEV + 2; ++l)
+            if (int64_t(hh[l]) != (l <= AMR_MAXLEV ? cnt[l] : 0)) return AMR_EINVAL;
+    }
     k_keys<<<nb, TB, 0, st>>>(lxyz, n, sk0, id0, err);
     size_t cb = W.cub_bytes;
     AMR_CUDA_TRY(cub::DeviceRadixSort::SortPairs(cubtmp, cb, sk0, sk1, id0, id1, (int)n, 0, 64, st));
@@ -595,4 +602,69 @@ extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oc
     AMR_CUDA_TRY(cudaGetLastError());
     if (herr != 0) return amr_status(herr);
     return AMR_OK;
+}
+
+extern "C" amr_status amr_build_octree(const amr_geom *geom, const int32_t *h_oct_lxyz, int64_t n,
+                                       void *d_tree_mem, size_t tree_bytes, void *d_workspace,
+                                       size_t workspace_bytes, amr_tree *out, amr_stream stream)
+{
+    if (geom && geom->n_inst > 0) {
+        if (!d_tree_mem || !d_workspace || !out) return AMR_EINVAL;
+        for (int f = 0; f < 6; ++f)
+            if (geom->bc[f] != AMR_BC_PERIODIC && geom->bc[f] != AMR_BC_OUTFLOW) return AMR_EINVAL;
+        for (int a = 0; a < 3; ++a)
+            if ((geom->bc[2 * a] == AMR_BC_PERIODIC) != (geom->bc[2 * a + 1] == AMR_BC_PERIODIC)) return AMR_EINVAL;
+        if ((uintptr_t(d_tree_mem) & 255) || (uintptr_t(d_workspace) & 255)) return AMR_EINVAL;
+        return build_boxes(geom, d_tree_mem, tree_bytes, d_workspace, workspace_bytes, out,
+                           reinterpret_cast<cudaStream_t>(stream));
+    }
+    if (check_geom(geom, n) != AMR_OK || !h_oct_lxyz || !d_tree_mem || !d_workspace || !out) return AMR_EINVAL;
+    if ((uintptr_t(d_tree_mem) & 255) || (uintptr_t(d_workspace) & 255)) return AMR_EINVAL;
+    int64_t cnt[AMR_MAXLEV + 2];
+    int lmax;
+    if (count_levels(h_oct_lxyz, n, cnt, &lmax) != AMR_OK) return AMR_EINVAL;
+    return build_tree(geom, h_oct_lxyz, nullptr, n, cnt, lmax, d_tree_mem, tree_bytes, d_workspace, workspace_bytes,
+                      out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+static amr_status device_counts(const amr_geom *geom, const int64_t *h_level_counts, int64_t cnt[AMR_MAXLEV + 2],
+                                int64_t *n, int *lmax)
+{
+    if (!geom || geom->n_inst != 0 || !h_level_counts) return AMR_EINVAL;
+    *n = 0;
+    *lmax = 0;
+    for (int l = 0; l < AMR_MAXLEV + 2; ++l) {
+        cnt[l] = l <= AMR_MAXLEV ? h_level_counts[l] : 0;
+        if (cnt[l] < 0 || (cnt[l] > 0 && (l < 1 || l > LMAX_BUILD))) return AMR_EINVAL;
+        if (cnt[l] > 0) *lmax = l;
+        *n += cnt[l];
+    }
+    return check_geom(geom, *n);
+}
+
+extern "C" amr_status amr_build_octree_device_query(const amr_geom *geom, const int64_t *h_level_counts,
+                                                    size_t *tree_bytes, size_t *workspace_bytes)
+{
+    int64_t cnt[AMR_MAXLEV + 2], n;
+    int lmax;
+    if (!tree_bytes || !workspace_bytes || device_counts(geom, h_level_counts, cnt, &n, &lmax) != AMR_OK)
+        return AMR_EINVAL;
+    if (lmax < geom->levelmin) return AMR_EINVAL;
+    *tree_bytes = tree_layout(n, cnt, geom->levelmin, lmax).total;
+    *workspace_bytes = ws_layout(n).total;
+    return AMR_OK;
+}
+
+extern "C" amr_status amr_build_octree_device(const amr_geom *geom, const int32_t *d_oct_lxyz,
+                                              const int64_t *h_level_counts, void *d_tree_mem, size_t tree_bytes,
+                                              void *d_workspace, size_t workspace_bytes, amr_tree *out,
+                                              amr_stream stream)
+{
+    int64_t cnt[AMR_MAXLEV + 2], n;
+    int lmax;
+    if (device_counts(geom, h_level_counts, cnt, &n, &lmax) != AMR_OK) return AMR_EINVAL;
+    if (!d_oct_lxyz || !d_tree_mem || !d_workspace || !out) return AMR_EINVAL;
+    if ((uintptr_t(d_tree_mem) & 255) || (uintptr_t(d_workspace) & 255)) return AMR_EINVAL;
+    return build_tree(geom, nullptr, d_oct_lxyz, n, cnt, lmax, d_tree_mem, tree_bytes, d_workspace, workspace_bytes,
+                      out, reinterpret_cast<cudaStream_t>(stream));
 }

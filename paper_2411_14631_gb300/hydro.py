@@ -67,6 +67,48 @@ class Octree:
     def n_inst(self):
         return int(self.t.n_inst)
 
+    def refine(self, u, mass_thr, levelmax, stream=None):
+        """refine_fine: the refined tree and the state on it.  Cells with rho dx^3 >
+        mass_thr are refined (levels levelmin .. levelmax-1), then 2:1-balanced; the new
+        oct list stays on the device, the new tree is built from it and the state is
+        copied or interpolated (amr_refine, amr_build_octree_device, amr_remap_state)."""
+        L = lib()
+        rp = abi.RefineParams(float(mass_thr), int(levelmax), 0)
+        wb = L.amr_refine_work_bytes(C.byref(self.t))
+        work = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        cap = self.ncell + 1
+        lxyz = torch.empty((cap, 4), dtype=torch.int32, device=self.device)
+        counts = (C.c_int64 * (abi.MAXLEV + 1))()
+        n = C.c_int64()
+        check("amr_refine", L.amr_refine(C.byref(self.t), C.byref(rp), _ptr(u), _ptr(work), wb, _ptr(lxyz), cap,
+                                         counts, C.byref(n), _stream(stream)))
+        del work
+        new = Octree.__new__(Octree)
+        new.device = self.device
+        g = abi.AmrGeom(self.levelmin, (C.c_int32 * 6)(*self.t.bc))
+        tb, wsb = C.c_size_t(), C.c_size_t()
+        check("amr_build_octree_device_query",
+              L.amr_build_octree_device_query(C.byref(g), counts, C.byref(tb), C.byref(wsb)))
+        new.mem = torch.empty(tb.value, dtype=torch.uint8, device=self.device)
+        ws = torch.empty(wsb.value, dtype=torch.uint8, device=self.device)
+        new.t = abi.AmrTree()
+        check("amr_build_octree_device",
+              L.amr_build_octree_device(C.byref(g), _ptr(lxyz), counts, _ptr(new.mem), tb.value, _ptr(ws), wsb.value,
+                                        C.byref(new.t), _stream(stream)))
+        del ws, lxyz
+        new.noct = int(new.t.noct)
+        new.ncell = 8 * new.noct
+        new.levelmin, new.levelmax = int(new.t.levelmin), int(new.t.levelmax)
+        new.lvl_off = np.array(new.t.lvl_off[:], dtype=np.int64)
+        u_new = torch.empty((5, new.ncell), dtype=torch.float64, device=self.device)
+        status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        check("amr_remap_state", L.amr_remap_state(C.byref(self.t), _ptr(u), C.byref(new.t), _ptr(u_new),
+                                                   _ptr(status), _stream(stream)))
+        st = int(status.item())
+        if st != abi.OK:
+            raise abi.AmrError("amr_remap_state", st)
+        return new, u_new
+
     def _view(self, ptr, n, dtype):
         off = ptr - self.mem.data_ptr()
         nbytes = n * torch.tensor([], dtype=dtype).element_size()

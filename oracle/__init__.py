@@ -18,7 +18,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = ["riemann.c", "tree.c", "hydro.c", "mlp.c", "box.c", "poisson.c", "refine.c"]
+_SRC = ["riemann.c", "tree.c", "hydro.c", "mlp.c", "box.c", "poisson.c", "refine.c", "subcycle.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 OK, EINVAL, EUNBALANCED, ENONPHYSICAL, ENOCONV, EBREAKDOWN = 0, -1, -2, -6, -7, -8
@@ -88,6 +88,8 @@ def lib():
         L.or_adam_step.argtypes = [P, P, P, P, C.c_int64, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_int64]
         I = C.c_int
+        L.or_courant_levels.argtypes = [P, P, P, P]
+        L.or_step_subcycled.argtypes = [P, P, P, P]
         L.or_refine_flags.argtypes = [P, P, C.c_double, I, P]
         L.or_refine_list.argtypes = [P, P, C.c_double, I, P, C.c_int64, C.POINTER(C.c_int64)]
         L.or_remap.argtypes = [P, P, P, P]
@@ -195,6 +197,19 @@ class Tree:
         dt = C.c_double()
         st = lib().or_step(self._h, C.byref(prm), _p(u), _p(un), C.byref(dt), nthreads)
         return un, dt.value, st
+
+    def step_subcycled(self, u, prm):
+        """One coarse step with sub-cycled levels (dt halves per level); returns (u, dt_base, status)."""
+        u = _f64(u).copy()
+        dt = C.c_double()
+        st = lib().or_step_subcycled(self._h, C.byref(prm), _p(u), C.byref(dt))
+        return u, dt.value, st
+
+    def courant_levels(self, u, prm):
+        u = _f64(u)
+        dt = C.c_double()
+        lib().or_courant_levels(self._h, C.byref(prm), _p(u), C.byref(dt))
+        return dt.value
 
     def level_update(self, level, u_old, u_new, reg, dt, prm):
         return lib().or_level_update(self._h, C.byref(prm), level, _p(u_old), _p(u_new), _p(reg), dt)

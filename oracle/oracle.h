@@ -97,6 +97,10 @@ void or_mlp_backward(const double *theta, const double *x, const double *dy, int
 void or_adam_step(double *th, double *m, double *v, const double *grad, int64_t n, double lr,
                   double beta1, double beta2, double eps, int64_t t);
 
+/* one coarse step with level sub-cycling, dt(l+1) = dt(l)/2 (subcycle.c); u in place */
+int or_courant_levels(const or_tree *t, const or_params *p, const double *u, double *dt_base);
+int or_step_subcycled(const or_tree *t, const or_params *p, double *u, double *dt_out);
+
 /* refinement between steps (refine.c) */
 int or_refine_flags(const or_tree *t, const double *u, double mass_thr, int lmax, uint8_t *flag /*[8 noct]*/);
 int or_refine_list(const or_tree *t, const double *u, double mass_thr, int lmax, int32_t *lxyz /*[cap][4]*/,

@@ -272,6 +272,30 @@ amr_status hydro_harvest_faces(const amr_tree *tree, const hydro_params *params,
                                const double *d_dt, double *d_states, int64_t capacity, int64_t stride,
                                unsigned long long *d_count, amr_stream stream);
 
+/* ---- sub-cycled step, dt(l+1) = dt(l)/2 -----------------------------------------------
+   Sec. 2.3 (the weights next to Eq. 1) sets sub-cycled levels, where level l+1 makes two
+   steps per step of level l, against one time step for all levels (hydro_step); the
+   paper prints no scheme.  The one computed here:
+     - dt_l = dt_base 2^-(l - levelmin); dt_base = C_cfl * min over leaves of
+       2^(l - levelmin) dx_l / sum_d (|u_d| + c) (hydro_courant_levels), so every level
+       runs at the same Courant number;
+     - coarse first: level c is advanced by dt_c, then level c+1 makes two steps of dt_c/2.
+       The first reads level-c ghosts at the start time T.  For the second, the leaves of
+       level c hold the mean of their states at T and T + dt_c plus the first fine
+       step's reflux correction (the coarse update carries no flux at faces next to
+       refined cells), and the refined cells of level c the mean of their children;
+     - after each fine step, coarse leaves next to refined cells take -/+ dt_{c+1}/dx_c
+       * 1/4 * sum of the fine fluxes; refined cells are restricted.
+   d_u: state, advanced in place by one step of the coarsest level; d_scratch: a second
+   state-sized buffer; d_flux_reg: hydro_flux_reg_bytes; d_dt: receives dt_base;
+   d_dt_levels: device double[AMR_MAXLEV + 2], receives dt_l.  Asynchronous, no host
+   synchronisation (capturable in a CUDA graph).  Octree mode only.  With one level it is
+   hydro_step with the same dt. */
+amr_status hydro_courant_levels(const amr_tree *t, const hydro_params *params, const double *d_u, double *d_dt,
+                                amr_stream stream);
+amr_status hydro_step_subcycled(const amr_tree *t, const hydro_params *params, double *d_u, double *d_scratch,
+                                double *d_flux_reg, double *d_dt, double *d_dt_levels, amr_stream stream);
+
 /* ---- refinement between steps (refine_fine, Table 1) ------------------------------
    The paper names the routine, not its rules.  The rules here:
      - a cell at level l, levelmin <= l < params->levelmax, is refined iff its mass

@@ -24,7 +24,7 @@ EXPORTS = ["amr_build_octree_query", "amr_build_octree", "hydro_init_from_prim",
            "mlp_grad", "mlp_train_step",
            "ppcg_workspace_bytes", "poisson_apply", "ppcg_start", "ppcg_iterate", "ppcg_poll", "ppcg_solve",
            "amr_refine_work_bytes", "amr_refine", "amr_build_octree_device_query", "amr_build_octree_device",
-           "amr_remap_state"]
+           "amr_remap_state", "hydro_courant_levels", "hydro_step_subcycled"]
 MLP_NPARAMS = 8962
 STATIC_REG_MAX_OCTS = 131072
 
@@ -104,6 +104,8 @@ def lib():
     L.mlp_forward.argtypes = [P, P, P, C.c_int64, P]
     L.mlp_grad.argtypes = [P, P, P, C.c_int64, P, P, S, P]
     L.mlp_train_step.argtypes = [P, P, P, P, P, P, C.c_int64, C.c_float, C.c_int64, P, P, S, P]
+    L.hydro_courant_levels.argtypes = [PT, PP, P, P, P]
+    L.hydro_step_subcycled.argtypes = [PT, PP, P, P, P, P, P, P]
     L.amr_refine_work_bytes.argtypes = [PT]
     L.amr_refine_work_bytes.restype = S
     L.amr_refine.argtypes = [PT, C.POINTER(RefineParams), P, P, S, P, C.c_int64, P, C.POINTER(C.c_int64), P]

@@ -24,8 +24,10 @@ __device__ __forceinline__ void min_to(double *target, double v)
 }
 
 template <typename R>
+// lscale >= 0: each leaf's candidate is multiplied by 2^(l - lscale), the coarsest
+// level's step that gives this leaf its own step dt 2^-(l - lscale) (sub-cycling)
 __global__ void k_courant(TreeView tv, int64_t cell0, const double *__restrict__ u, double gamma, double rf,
-                          double pf, double cfl, double *dt)
+                          double pf, double cfl, double *dt, int lscale)
 {
     const int64_t cell = cell0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     double cand = DBL_MAX;
@@ -35,9 +37,30 @@ __global__ void k_courant(TreeView tv, int64_t cell0, const double *__restrict__
         for (int v = 0; v < NV; ++v) U[v] = u[v * tv.ncell + cell];
         Prm<R> p;
         p.gamma = to_work<R>(gamma); p.rho_floor = to_work<R>(rf); p.p_floor = to_work<R>(pf);
-        cand = cfl_candidate<R>(U, p, to_work<R>(cfl), to_work<R>(pow2(-tv.lvl[cell >> 3])));
+        const int l = tv.lvl[cell >> 3];
+        cand = cfl_candidate<R>(U, p, to_work<R>(cfl), to_work<R>(pow2(-l)));
+        if (lscale >= 0) cand = scale_pow2(cand, l - lscale);
     }
     min_to(dt, cand);
+}
+
+// sub-cycling: the step of every level from the coarsest level's step
+__global__ void k_dt_levels(const double *__restrict__ dt_base, int levelmin, double *dtl)
+{
+    const int l = threadIdx.x;
+    if (l < AMR_MAXLEV + 2) dtl[l] = l > levelmin ? scale_pow2(*dt_base, levelmin - l) : *dt_base;
+}
+
+// sub-cycling: leaves of one level take the mean of two states (time interpolation)
+__global__ void k_lerp_leaves(TreeView tv, int level, double *U, const double *__restrict__ N)
+{
+    const int64_t cell = tv.lvl_off[level] * 8 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (cell >= tv.lvl_off[level + 1] * 8 || tv.son[cell] >= 0) return;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const int64_t i = v * tv.ncell + cell;
+        U[i] = 0.5 * (U[i] + N[i]);
+    }
 }
 
 // batch mode: per-box CFL step (box cell ranges are multiples of 64, so a warp never
@@ -238,9 +261,9 @@ extern "C" amr_status hydro_courant(const amr_tree *t, const hydro_params *p, co
     const int64_t c0 = t->lvl_off[t->levelmin] * 8, nc = 8 * t->noct - c0;
     const unsigned nb = unsigned((nc + 255) / 256);
     if (p->precision == AMR_PREC_FP32)
-        k_courant<float><<<nb, 256, 0, st>>>(tv, c0, d_u, p->gamma, p->rho_floor, p->p_floor, p->cfl, d_dt);
+        k_courant<float><<<nb, 256, 0, st>>>(tv, c0, d_u, p->gamma, p->rho_floor, p->p_floor, p->cfl, d_dt, -1);
     else
-        k_courant<double><<<nb, 256, 0, st>>>(tv, c0, d_u, p->gamma, p->rho_floor, p->p_floor, p->cfl, d_dt);
+        k_courant<double><<<nb, 256, 0, st>>>(tv, c0, d_u, p->gamma, p->rho_floor, p->p_floor, p->cfl, d_dt, -1);
     AMR_CUDA_TRY(cudaGetLastError());
     return AMR_OK;
 }
@@ -268,6 +291,71 @@ extern "C" amr_status hydro_reflux_level(const amr_tree *t, int level, const hyd
     if (level < 1 || level >= t->levelmax) return AMR_EINVAL;
     if (level >= t->levelmin && !d_flux_reg) return AMR_EINVAL;
     return reflux_launch(t, level, p, d_flux_reg, d_u_new, d_dt, d_dt_next, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---- sub-cycled step -----------------------------------------------------------------
+static amr_status sc_advance(const amr_tree *t, const hydro_params *p, int c, double *U, double *N, double *reg,
+                             double *dtl, cudaStream_t st)
+{
+    amr_status r = hydro_godunov_level(t, c, p, U, N, reg, dtl + c, nullptr, reinterpret_cast<amr_stream>(st));
+    if (r != AMR_OK) return r;
+    if (c < t->levelmax) {
+        if ((r = sc_advance(t, p, c + 1, U, N, reg, dtl, st)) != AMR_OK) return r;
+        // ghosts of the second fine step: coarse leaves interpolated in time plus the first
+        // fine step's correction; refined cells restricted from the fine level
+        const int64_t nc = (t->lvl_off[c + 1] - t->lvl_off[c]) * 8;
+        if (nc > 0) {
+            k_lerp_leaves<<<unsigned((nc + 255) / 256), 256, 0, st>>>(make_view(t), c, U, N);
+            AMR_CUDA_TRY(cudaGetLastError());
+        }
+        if ((r = reflux_launch(t, c, p, reg, U, dtl + c + 1, nullptr, st, 1)) != AMR_OK) return r;
+        if ((r = reflux_launch(t, c, p, reg, N, dtl + c + 1, nullptr, st, 0)) != AMR_OK) return r;
+        if ((r = sc_advance(t, p, c + 1, U, N, reg, dtl, st)) != AMR_OK) return r;
+        if ((r = reflux_launch(t, c, p, reg, N, dtl + c + 1, nullptr, st, 0)) != AMR_OK) return r;
+    }
+    // the level's new state becomes current (its cells are contiguous in each variable)
+    const int64_t c0 = t->lvl_off[c] * 8, n = (t->lvl_off[c + 1] - t->lvl_off[c]) * 8, ncell = 8 * t->noct;
+    if (n > 0)
+        for (int v = 0; v < NV; ++v)
+            AMR_CUDA_TRY(cudaMemcpyAsync(U + v * ncell + c0, N + v * ncell + c0, size_t(n) * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+    return AMR_OK;
+}
+
+extern "C" amr_status hydro_courant_levels(const amr_tree *t, const hydro_params *p, const double *d_u, double *d_dt,
+                                           amr_stream stream)
+{
+    if (check(t, p) != AMR_OK || !d_u || !d_dt || t->n_inst != 0) return AMR_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const TreeView tv = make_view(t);
+    AMR_CUDA_TRY(cudaMemsetAsync(d_dt, 0x7F, sizeof(double), st));
+    const int64_t c0 = t->lvl_off[t->levelmin] * 8, nc = 8 * t->noct - c0;
+    const unsigned nb = unsigned((nc + 255) / 256);
+    if (p->precision == AMR_PREC_FP32)
+        k_courant<float><<<nb, 256, 0, st>>>(tv, c0, d_u, p->gamma, p->rho_floor, p->p_floor, p->cfl, d_dt,
+                                             t->levelmin);
+    else
+        k_courant<double><<<nb, 256, 0, st>>>(tv, c0, d_u, p->gamma, p->rho_floor, p->p_floor, p->cfl, d_dt,
+                                              t->levelmin);
+    AMR_CUDA_TRY(cudaGetLastError());
+    return AMR_OK;
+}
+
+extern "C" amr_status hydro_step_subcycled(const amr_tree *t, const hydro_params *p, double *d_u, double *d_scratch,
+                                           double *d_flux_reg, double *d_dt, double *d_dt_levels, amr_stream stream)
+{
+    if (check(t, p) != AMR_OK || t->n_inst != 0 || !d_u || !d_scratch || !d_dt || !d_dt_levels || d_u == d_scratch)
+        return AMR_EINVAL;
+    if (t->levelmax > t->levelmin && !d_flux_reg) return AMR_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    amr_status r = hydro_courant_levels(t, p, d_u, d_dt, stream);
+    if (r != AMR_OK) return r;
+    k_dt_levels<<<1, 32, 0, st>>>(d_dt, t->levelmin, d_dt_levels);
+    AMR_CUDA_TRY(cudaGetLastError());
+    if ((r = sc_advance(t, p, t->levelmin, d_u, d_scratch, d_flux_reg, d_dt_levels, st)) != AMR_OK) return r;
+    for (int l = t->levelmin - 1; l >= 1; --l)
+        if ((r = reflux_launch(t, l, p, nullptr, d_u, d_dt_levels, nullptr, st, 1)) != AMR_OK) return r;
+    return AMR_OK;
 }
 
 extern "C" amr_status hydro_step(const amr_tree *t, const hydro_params *p, const double *d_u_old, double *d_u_new,

@@ -281,6 +281,59 @@ class Surrogate:
         return hist
 
 
+def hydro_courant_levels(tree, prm, u, dt, stream=None):
+    check("hydro_courant_levels", lib().hydro_courant_levels(C.byref(tree.t), C.byref(prm.c), _ptr(u), _ptr(dt),
+                                                             _stream(stream)))
+
+
+def hydro_step_subcycled(tree, prm, u, scratch, reg, dt, dt_levels, stream=None):
+    check("hydro_step_subcycled",
+          lib().hydro_step_subcycled(C.byref(tree.t), C.byref(prm.c), _ptr(u), _ptr(scratch), _ptr(reg), _ptr(dt),
+                                     _ptr(dt_levels), _stream(stream)))
+
+
+class SubcycledSimulation:
+    """A run with sub-cycled levels: each ``step()`` advances the coarsest level by its
+    step and every finer level by 2^(l - levelmin) steps of half the previous size
+    (hydro_step_subcycled); ``dt`` holds the coarsest level's last step on the device."""
+
+    def __init__(self, tree, prm, w0=None, u0=None):
+        self.tree, self.prm = tree, prm
+        dev = tree.device
+        self.u = torch.empty((5, tree.ncell), dtype=torch.float64, device=dev)
+        self.scratch = torch.empty_like(self.u)
+        self.reg = torch.zeros(max(1, tree.flux_reg_bytes() // 8), dtype=torch.float64, device=dev)
+        self.dt = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.dt_levels = torch.zeros(abi.MAXLEV + 2, dtype=torch.float64, device=dev)
+        if u0 is not None:
+            self.u.copy_(u0)
+        else:
+            w = torch.as_tensor(np.ascontiguousarray(w0), dtype=torch.float64).to(dev)
+            hydro_init_from_prim(tree, prm, w, self.u)
+        self.nsteps = 0
+        self._graph = None
+
+    def step(self, stream=None):
+        if self._graph is not None:
+            self._graph.replay()
+        else:
+            hydro_step_subcycled(self.tree, self.prm, self.u, self.scratch, self.reg, self.dt, self.dt_levels, stream)
+        self.nsteps += 1
+
+    def use_graph(self):
+        """Capture one step in a CUDA graph (the buffers do not alternate)."""
+        self.step()
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream(device=self.tree.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            hydro_step_subcycled(self.tree, self.prm, self.u, self.scratch, self.reg, self.dt, self.dt_levels,
+                                 stream=s)
+        self._graph = g
+        torch.cuda.synchronize()
+        return self
+
+
 class Simulation:
     """State buffers and the step sequence of one run (u_old -> u_new, dt on the device).
 

@@ -56,6 +56,7 @@ typedef enum {
 enum { AMR_BC_PERIODIC = 0, AMR_BC_OUTFLOW = 1 };
 enum { AMR_RIEMANN_HLLC = 0, AMR_RIEMANN_EXACT = 1, AMR_RIEMANN_MLP = 2, AMR_RIEMANN_MLP_SEEDED = 3 };
 enum { AMR_PREC_FP64 = 0, AMR_PREC_FP32 = 1 };
+enum { AMR_LIMITER_MINMOD = 0, AMR_LIMITER_MC = 1 };
 
 #define AMR_MAXLEV 21
 #define AMR_NCOUNTERS 8
@@ -80,6 +81,8 @@ typedef struct {
    mlp_weights: device pointer to the surrogate's weights (AMR_RIEMANN_MLP and
    AMR_RIEMANN_MLP_SEEDED only);
    mlp_resid_tol: acceptance threshold of the surrogate's residual check;
+   limiter: slopes of the reconstruction, AMR_LIMITER_MINMOD (MinMod) or AMR_LIMITER_MC
+   (monotonized central, van Leer 1977; updated by the tile kernel on every level);
    d_status: device int32 error word (may be NULL); d_counters: device uint64
    counters[AMR_NCOUNTERS] (may be NULL), accumulated over calls: [0] faces solved by the
    surrogate (AMR_RIEMANN_MLP) or whose Newton solve it seeded (AMR_RIEMANN_MLP_SEEDED),
@@ -90,7 +93,8 @@ typedef struct {
     double gamma, cfl, rho_floor, p_floor;
     int32_t riemann, precision, tile, tiles_only;
     const void *mlp_weights;
-    float mlp_resid_tol, reserved_f;
+    float mlp_resid_tol;
+    int32_t limiter;
     int32_t *d_status;
     unsigned long long *d_counters;
 } hydro_params;

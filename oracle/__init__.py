@@ -64,6 +64,8 @@ def lib():
         L.or_lookup.argtypes = [P, C.c_int, C.c_int64, C.c_int64, C.c_int64]
         L.or_minmod.restype = C.c_double
         L.or_minmod.argtypes = [C.c_double, C.c_double]
+        L.or_mc.restype = C.c_double
+        L.or_mc.argtypes = [C.c_double, C.c_double]
         L.or_cons_to_prim.argtypes = [P, C.c_double, C.c_double, C.c_double, P]
         L.or_prim_to_cons.argtypes = [P, C.c_double, P]
         L.or_flux_normal.argtypes = [P, C.c_double, P]
@@ -111,11 +113,14 @@ def _f64(a):
 
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("rho_floor", C.c_double),
-                ("p_floor", C.c_double), ("riemann", C.c_int32), ("pad", C.c_int32)]
+                ("p_floor", C.c_double), ("riemann", C.c_int32), ("limiter", C.c_int32)]
 
 
-def params(gamma=1.4, cfl=0.8, rho_floor=1e-10, p_floor=1e-20, riemann=HLLC):
-    return Params(gamma, cfl, rho_floor, p_floor, riemann, 0)
+LIMITER_MINMOD, LIMITER_MC = 0, 1
+
+
+def params(gamma=1.4, cfl=0.8, rho_floor=1e-10, p_floor=1e-20, riemann=HLLC, limiter=LIMITER_MINMOD):
+    return Params(gamma, cfl, rho_floor, p_floor, riemann, limiter)
 
 
 class Tree:
@@ -254,6 +259,10 @@ def hilbert_key(bits, x, y, z):
 
 def minmod(a, b):
     return lib().or_minmod(a, b)
+
+
+def mc(a, b):
+    return lib().or_mc(a, b)
 
 
 def cons_to_prim(U, gamma, rho_floor=1e-10, p_floor=1e-20):

@@ -82,8 +82,8 @@ int or_box_step(int64_t N, const int32_t *bc, const or_params *p, const double *
                 for (int v = 0; v < NV; v++) Wc[v] = W[(int64_t)v * ne + s];
                 for (int d = 0; d < 3; d++)
                     for (int v = 0; v < NV; v++)
-                        D[d][v] = or_minmod(W[(int64_t)v * ne + s] - W[(int64_t)v * ne + s - step[d]],
-                                            W[(int64_t)v * ne + s + step[d]] - W[(int64_t)v * ne + s]);
+                        D[d][v] = or_slope(p->limiter, W[(int64_t)v * ne + s] - W[(int64_t)v * ne + s - step[d]],
+                                           W[(int64_t)v * ne + s + step[d]] - W[(int64_t)v * ne + s]);
                 predict_cell(Wc, D, p->gamma, lam, Wt);
                 for (int d = 0; d < 3; d++)
                     for (int side = 0; side < 2; side++) {

@@ -14,7 +14,8 @@
  *   - boundaries: periodic wraps, outflow clamps the integer cell coordinate at the
  *     cell's own level (zero gradient);
  *   - MUSCL-Hancock in primitive variables (Toro 2009, Sec. 14.4): MinMod slopes of
- *     undivided differences, the half-step predictor written out in or_predict below,
+ *     undivided differences (or, on request, the monotonized central limiter of van
+ *     Leer 1977), the half-step predictor written out in or_predict below,
  *     face states W~ +- Delta/2 with rho and p floored;
  *   - Riemann problem at each face in the face-normal frame (HLLC or exact);
  *   - conservative FP64 update U += dt/dx * sum_d (F_{d,-} - F_{d,+});
@@ -171,7 +172,8 @@ static int oct_update(const or_tree *t, const or_params *p, int64_t oct, const d
                 for (int v = 0; v < NV; v++) W[v] = wk->W[v][s];
                 for (int d = 0; d < 3; d++)
                     for (int v = 0; v < NV; v++)
-                        D[d][v] = or_minmod(wk->W[v][s] - wk->W[v][s - step[d]], wk->W[v][s + step[d]] - wk->W[v][s]);
+                        D[d][v] = or_slope(p->limiter, wk->W[v][s] - wk->W[v][s - step[d]],
+                                           wk->W[v][s + step[d]] - wk->W[v][s]);
                 or_predict(W, D, p->gamma, lam, Wt);
                 for (int d = 0; d < 3; d++)
                     for (int side = 0; side < 2; side++) {

@@ -46,10 +46,12 @@ typedef struct {
     int64_t *lex;                 /* oct ids sorted by (lvl, ix, iy, iz) for lookups */
 } or_tree;
 
+enum { OR_LIMITER_MINMOD = 0, OR_LIMITER_MC = 1 };
+
 typedef struct {
     double gamma, cfl, rho_floor, p_floor;
     int32_t riemann;              /* OR_HLLC or OR_EXACT */
-    int32_t pad;
+    int32_t limiter;              /* slopes of the reconstruction: OR_LIMITER_MINMOD or OR_LIMITER_MC */
 } or_params;
 
 uint64_t or_hilbert_key(int bits, uint32_t x, uint32_t y, uint32_t z);
@@ -63,6 +65,8 @@ int64_t or_lookup(const or_tree *t, int l, int64_t x, int64_t y, int64_t z);
 
 /* single-state pieces */
 double or_minmod(double a, double b);
+double or_mc(double a, double b);
+double or_slope(int limiter, double a, double b);
 void or_cons_to_prim(const double *U, double gamma, double rho_floor, double p_floor, double *W);
 void or_prim_to_cons(const double *W, double gamma, double *U);
 void or_flux_normal(const double *W, double gamma, double *F);

@@ -21,6 +21,20 @@ double or_minmod(double a, double b)
     return fabs(a) < fabs(b) ? a : b;
 }
 
+double or_mc(double a, double b)
+{
+    /* monotonized central (van Leer 1977): zero at an extremum, otherwise the central
+       difference (a+b)/2 limited to twice either one-sided difference */
+    if (a * b <= 0.0) return 0.0;
+    double m = fmin(fmin(2.0 * fabs(a), 2.0 * fabs(b)), 0.5 * fabs(a + b));
+    return a > 0.0 ? m : -m;
+}
+
+double or_slope(int limiter, double a, double b)
+{
+    return limiter == OR_LIMITER_MC ? or_mc(a, b) : or_minmod(a, b);
+}
+
 void or_cons_to_prim(const double *U, double gamma, double rho_floor, double p_floor, double *W)
 {
     double rho = U[0] > rho_floor ? U[0] : rho_floor;

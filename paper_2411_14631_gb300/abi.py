@@ -14,6 +14,7 @@ OK, EINVAL, EUNBALANCED, ECAPACITY, ECUDA, ETIMEOUT, ENONPHYSICAL, ENOCONV, EBRE
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 RIEMANN_HLLC, RIEMANN_EXACT, RIEMANN_MLP, RIEMANN_MLP_SEEDED = 0, 1, 2, 3
 PREC_FP64, PREC_FP32 = 0, 1
+LIMITER_MINMOD, LIMITER_MC = 0, 1
 PRECOND_NONE, PRECOND_IP = 0, 1
 OP_A, OP_MINV = 0, 1
 
@@ -36,7 +37,7 @@ class AmrGeom(C.Structure):
 class HydroParams(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("rho_floor", C.c_double), ("p_floor", C.c_double),
                 ("riemann", C.c_int32), ("precision", C.c_int32), ("tile", C.c_int32), ("tiles_only", C.c_int32),
-                ("mlp_weights", C.c_void_p), ("mlp_resid_tol", C.c_float), ("reserved_f", C.c_float),
+                ("mlp_weights", C.c_void_p), ("mlp_resid_tol", C.c_float), ("limiter", C.c_int32),
                 ("d_status", C.c_void_p), ("d_counters", C.c_void_p)]
 
 

@@ -50,6 +50,7 @@ struct GArgs {
     const void *mlp;          // packed surrogate weights (RS == AMR_RIEMANN_MLP)
     float mlp_tol;            // residual acceptance threshold
     int32_t mlp_seed;         // 1: the network's p* seeds Newton at every face (no acceptance test)
+    int32_t limiter;          // AMR_LIMITER_* of the slopes
     double *harvest;          // if set: sampled face states [cap][6] are written, u_new is not
     int64_t harvest_cap, harvest_stride;
     unsigned long long *harvest_count;
@@ -337,6 +338,7 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
     const int tid = threadIdx.x;
     Prm<R> pr;
     pr.gamma = to_work<R>(a.gamma); pr.rho_floor = to_work<R>(a.rho_floor); pr.p_floor = to_work<R>(a.p_floor);
+    pr.limiter = a.limiter;
     const R cflR = to_work<R>(a.cfl);
 
     unsigned n_acc = 0, n_fb = 0;   // surrogate: accepted faces, fallbacks (counted by lane 0)
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
             for (int d = 0; d < 3; ++d)
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
-                    Dl[d][v] = minmod(Wc[v] - sm.W[v][si - st[d]], sm.W[v][si + st[d]] - Wc[v]);
+                    Dl[d][v] = slope(pr, Wc[v] - sm.W[v][si - st[d]], sm.W[v][si + st[d]] - Wc[v]);
             const R r = Wc[0], u = Wc[1], vv = Wc[2], w = Wc[3], pp = Wc[4];
             R Wt[NV];
             Wt[0] = r - hl * (u * Dl[0][0] + r * Dl[0][1] + vv * Dl[1][0] + r * Dl[1][2] + w * Dl[2][0] + r * Dl[2][3]);
@@ -605,12 +607,14 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
     int depth = p->tile == 0 ? 1 : p->tile;
     if (depth != 1 && depth != 2) return AMR_EINVAL;
     const bool mlp_like = p->riemann == AMR_RIEMANN_MLP || p->riemann == AMR_RIEMANN_MLP_SEEDED;
+    // the z-column kernel implements MinMod slopes; the MC limiter runs in the tile kernel
+    const bool col_ok = !p->tiles_only && !mlp_like && p->limiter == AMR_LIMITER_MINMOD;
     if (depth == 2 && sizeof(R) == 8) return AMR_EINVAL;   // an FP64 12^3-cell stencil does not fit in smem
     if (t->n_inst > 0) {
         // batch mode: every box in one launch (z-column kernel when every box is a multiple of
         // 16 cells, else tiles)
         if (level != -1) return AMR_EINVAL;
-        if (!p->tiles_only && !mlp_like && t->col_work > 0)
+        if (col_ok && t->col_work > 0)
             return p->riemann == AMR_RIEMANN_EXACT
                        ? launch_col<R, AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, st)
                        : launch_col<R, AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, st);
@@ -630,6 +634,7 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
         a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
         a.status = p->d_status; a.counters = p->d_counters;
         a.mlp = p->mlp_weights; a.mlp_tol = p->mlp_resid_tol; a.mlp_seed = p->riemann == AMR_RIEMANN_MLP_SEEDED;
+        a.limiter = p->limiter;
         a.harvest = nullptr; a.harvest_cap = 0; a.harvest_stride = 1; a.harvest_count = nullptr;
         const int64_t nt = a.t_end;
         constexpr int D2 = 2 - (sizeof(R) == 8);
@@ -648,7 +653,7 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
     // the deepest complete level goes to the z-column kernel (bitwise the same per cell);
     // the levels below and above it to the tile kernel
     const int gl = t->grid_level;
-    if (!p->tiles_only && !mlp_like && t->grid && gl >= 3 && gl >= l0 && gl <= l1) {
+    if (col_ok && t->grid && gl >= 3 && gl >= l0 && gl <= l1) {
         const amr_status r = p->riemann == AMR_RIEMANN_EXACT
                                  ? launch_col<R, AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, st)
                                  : launch_col<R, AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, st);
@@ -683,6 +688,7 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
         a.mlp = p->mlp_weights;
         a.mlp_tol = p->mlp_resid_tol;
         a.mlp_seed = p->riemann == AMR_RIEMANN_MLP_SEEDED;
+        a.limiter = p->limiter;
         a.harvest = nullptr;
         a.harvest_cap = 0;
         a.harvest_stride = 1;
@@ -728,7 +734,7 @@ inline amr_status harvest_impl(const amr_tree *t, const hydro_params *p, const d
     a.u_old = u; a.u_new = nullptr; a.reg = nullptr; a.dt = dt; a.dt_next = nullptr;
     a.gamma = p->gamma; a.rho_floor = p->rho_floor; a.p_floor = p->p_floor; a.cfl = p->cfl;
     a.status = p->d_status; a.counters = nullptr;
-    a.mlp = nullptr; a.mlp_tol = 0.0f; a.mlp_seed = 0;
+    a.mlp = nullptr; a.mlp_tol = 0.0f; a.mlp_seed = 0; a.limiter = p->limiter;
     a.harvest = out; a.harvest_cap = cap; a.harvest_stride = stride; a.harvest_count = count;
     return launch<double, 1, AMR_RIEMANN_HLLC>(a, a.t_end - a.t_begin, st);
 }

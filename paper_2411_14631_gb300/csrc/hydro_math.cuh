@@ -41,6 +41,7 @@ __device__ __forceinline__ double to_state(float x) { return f2d_bits(x); }
 
 template <typename R> struct Prm {
     R gamma, rho_floor, p_floor;
+    int limiter = AMR_LIMITER_MINMOD;   // slopes of the reconstruction
 };
 
 // MinMod: zero when the differences disagree in sign, else the smaller magnitude (equal
@@ -52,6 +53,20 @@ template <typename R> __device__ __forceinline__ R minmod(R a, R b)
 }
 
 template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+
+// Monotonized central limiter (van Leer 1977): zero when the differences disagree in
+// sign, else the central difference (a+b)/2 limited to twice either difference
+template <typename R> __device__ __forceinline__ R mc_limit(R a, R b)
+{
+    const R m = fmin(fmin(R(2) * fabs(a), R(2) * fabs(b)), R(0.5) * fabs(a + b));
+    return a * b > R(0) ? copysign(m, a) : R(0);
+}
+
+// slope of the reconstruction from the two one-sided differences
+template <typename R> __device__ __forceinline__ R slope(const Prm<R> &p, R a, R b)
+{
+    return p.limiter == AMR_LIMITER_MC ? mc_limit(a, b) : minmod(a, b);
+}
 
 // conserved (FP64 storage) -> primitive in precision R, floors applied
 template <typename R>

@@ -184,6 +184,7 @@ static amr_status check(const amr_tree *t, const hydro_params *p)
     if (p->riemann < AMR_RIEMANN_HLLC || p->riemann > AMR_RIEMANN_MLP_SEEDED) return AMR_EINVAL;
     if (p->precision != AMR_PREC_FP64 && p->precision != AMR_PREC_FP32) return AMR_EINVAL;
     if (p->tile < 0 || p->tile > 2) return AMR_EINVAL;
+    if (p->limiter != AMR_LIMITER_MINMOD && p->limiter != AMR_LIMITER_MC) return AMR_EINVAL;
     return AMR_OK;
 }
 

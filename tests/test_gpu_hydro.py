@@ -38,15 +38,15 @@ def _smooth_random(xyz, seed, amp=0.3):
     return Wp
 
 
-def _pair(oracle, H, lx, levelmin, bc, prims, gamma, cfl=0.8, riemann=0, precision=0, tile=0):
+def _pair(oracle, H, lx, levelmin, bc, prims, gamma, cfl=0.8, riemann=0, precision=0, tile=0, limiter=0):
     import torch
     t = oracle.Tree(lx, levelmin, bc)
     assert t.ok
     g = H.Octree(lx, levelmin, bc)
     xyz, _ = t.cell_centres()
     w0 = prims(xyz)
-    prm_o = oracle.params(gamma=gamma, cfl=cfl, riemann=riemann)
-    prm_g = H.Params(gamma, cfl=cfl, riemann=riemann, precision=precision, tile=tile)
+    prm_o = oracle.params(gamma=gamma, cfl=cfl, riemann=riemann, limiter=limiter)
+    prm_g = H.Params(gamma, cfl=cfl, riemann=riemann, precision=precision, tile=tile, limiter=limiter)
     u_o = t.init_from_prim(w0, prm_o)
     sim = H.Simulation(g, prm_g, w0=w0)
     torch.cuda.synchronize()
@@ -129,6 +129,24 @@ def test_amr_fp64_parity(oracle, H, seed, periodic):
         assert abs(dt_o - dt_g) <= 1e-14 * dt_o
     err = _relerr(u_g, u_o)
     assert np.all(err <= FP64_TOL), err
+
+
+@pytest.mark.parametrize("seed,periodic", [(0, True), (1, False)])
+def test_mc_limiter_fp64_parity(oracle, H, seed, periodic):
+    """The monotonized central limiter (tile kernel on every level), FP64 against the oracle
+    on random AMR trees; a uniform 16^3 box exercises the level the z-column kernel would
+    take with MinMod."""
+    lx = W.random_tree(3, 3, 60 + seed, p_refine=0.3, periodic=periodic)
+    t, g, prm_o, prm_g, u_o, sim = _pair(oracle, H, lx, 3, PER if periodic else OUT,
+                                        lambda x: _smooth_random(x, seed), 5 / 3, cfl=0.6, limiter=1)
+    u_o, u_g, dts = _run_both(t, prm_o, u_o, sim, 4)
+    for dt_o, dt_g in dts:
+        assert abs(dt_o - dt_g) <= 1e-14 * dt_o
+    assert np.all(_relerr(u_g, u_o) <= FP64_TOL), _relerr(u_g, u_o)
+    t, g, prm_o, prm_g, u_o, sim = _pair(oracle, H, W.uniform_tree(4), 4, OUT, lambda x: W.sod_prims(x), 1.4,
+                                        limiter=1)
+    u_o, u_g, _ = _run_both(t, prm_o, u_o, sim, 10)
+    assert np.all(_relerr(u_g, u_o) <= FP64_TOL), _relerr(u_g, u_o)
 
 
 def test_exact_riemann_fp64_parity(oracle, H):

@@ -650,9 +650,13 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
     int l0 = level < 0 ? t->levelmin : level, l1 = level < 0 ? t->levelmax : level;
     if (level <= -2) { l0 = (-2 - level) & 255; l1 = (-2 - level) >> 8; }
     if (l0 < t->levelmin || l1 > t->levelmax) return AMR_EINVAL;
-    // the deepest complete level goes to the z-column kernel (bitwise the same per cell);
-    // the levels below and above it to the tile kernel
+    // levels below the deepest complete level have no leaf cells and no octs whose father
+    // this kernel restricts: nothing to update there
     const int gl = t->grid_level;
+    if (t->grid && gl > l0) l0 = gl;
+    if (l0 > l1) return AMR_OK;
+    // the deepest complete level goes to the z-column kernel (bitwise the same per cell);
+    // the levels above it to the tile kernel
     if (col_ok && t->grid && gl >= 3 && gl >= l0 && gl <= l1) {
         const amr_status r = p->riemann == AMR_RIEMANN_EXACT
                                  ? launch_col<R, AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, st)

@@ -154,11 +154,13 @@ __device__ int64_t cell_of(const BuildView &b, int l, int64_t X, int64_t Y, int6
     return o < 0 ? -1 : o * 8 + (X & 1) + 2 * (Y & 1) + 4 * (Z & 1);
 }
 
-__global__ void k_tables(BuildView b, int32_t *son, int32_t *father, int32_t *nbor, int32_t *nb27,
+// Tables by search (son, father, nbor, nb27, refmask) for the octs [0, o1): levels 1 and 2,
+// whose neighbours cannot come from a coarser oct's table (the root's has no wrap).
+__global__ void k_tables(BuildView b, int64_t o1, int32_t *son, int32_t *father, int32_t *nbor, int32_t *nb27,
                          uint8_t *refmask, int32_t *err)
 {
     const int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (o >= b.n) return;
+    if (o >= o1) return;
     const int l = b.lvl[o];
     const int64_t x = b.ix[o], y = b.iy[o], z = b.iz[o];
     uint32_t mask = 0;
@@ -205,6 +207,71 @@ __global__ void k_tables(BuildView b, int32_t *son, int32_t *father, int32_t *nb
 // An oct whose eight cells are leaves and have no refined same-level face neighbour:
 // its cells are final after the Godunov update (no reflux, no restriction reaches them),
 // so the update kernel can also restrict its father cell.
+// Every oct's father cell (one search) and, scattered from it, the son table.
+__global__ void k_father_son(BuildView b, int32_t *son, int32_t *father, int32_t *err)
+{
+    const int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (o >= b.n) return;
+    const int l = b.lvl[o];
+    if (l == 1) {
+        father[o] = -1;
+        return;
+    }
+    const int64_t f = cell_of(b, l - 1, b.ix[o], b.iy[o], b.iz[o]);
+    if (f < 0) set_error(err, AMR_EINVAL);                             // oct without its father cell
+    father[o] = int32_t(f);
+    if (f >= 0) son[f] = int32_t(o);
+}
+
+// Tables of the level-l octs (l >= 3) from the tables of their fathers' octs: the level-(l-1)
+// cell next to an oct's father lies in the father oct or one of its 26 neighbours, and the
+// level-l neighbour oct is that cell's son.  Same entries as k_tables, without searching.
+__global__ void k_tables_level(BuildView b, int l, const int32_t *__restrict__ son, const int32_t *__restrict__ father,
+                               int32_t *nbor, int32_t *nb27, uint8_t *refmask, int32_t *err)
+{
+    const int64_t o = b.lvl_off[l] + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (o >= b.lvl_off[l + 1]) return;
+    const int32_t x = b.ix[o], y = b.iy[o], z = b.iz[o];   // father cell coordinates (level l-1)
+    uint32_t mask = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (son[8 * o + c] >= 0) mask |= 1u << c;
+    refmask[o] = uint8_t(mask);
+    if (l < b.levelmin && mask != 0xFFu) set_error(err, AMR_EINVAL);   // levels below levelmin have no leaves
+    const int32_t f = father[o];
+    if (f < 0) return;                                                 // reported by k_father_son
+    const int32_t *pn = nb27 + 27 * int64_t(f >> 3);                   // the father's oct (level l-1)
+    // level-(l-1) cell (X, Y, Z) next to the father: its oct among the father oct's 27
+    auto cell_near = [&](int32_t X, int32_t Y, int32_t Z, int32_t &cid) -> int {
+        const int k = ((X >> 1) - (x >> 1) + 1) + 3 * ((Y >> 1) - (y >> 1) + 1) + 9 * ((Z >> 1) - (z >> 1) + 1);
+        const int32_t po = pn[k];
+        if (po == OUTSIDE) return 1;                                   // beyond an outflow face
+        if (po < 0) return 2;                                          // missing: 2:1 rule broken
+        cid = po * 8 + (X & 1) + 2 * (Y & 1) + 4 * (Z & 1);
+        return 0;
+    };
+    for (int k = 0; k < 6; ++k) {
+        int32_t P[3] = {x, y, z};
+        P[k >> 1] += (k & 1) ? 1 : -1;
+        int32_t cid = -1;
+        const int r = cell_near(P[0], P[1], P[2], cid);
+        if (r == 2) set_error(err, AMR_EUNBALANCED);
+        nbor[6 * o + k] = r == 0 ? cid : -1;
+    }
+    for (int k = 0; k < 27; ++k) {
+        const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+        int32_t cid = -1;
+        const int r = cell_near(x + dx, y + dy, z + dz, cid);
+        if (r != 0) {
+            if (r == 2) set_error(err, AMR_EUNBALANCED);
+            nb27[27 * o + k] = OUTSIDE;
+            continue;
+        }
+        const int32_t sn = son[cid];
+        nb27[27 * o + k] = sn >= 0 ? sn : -1 - cid;
+    }
+}
+
 __global__ void k_fused(BuildView b, const int32_t *__restrict__ son, const int32_t *__restrict__ nbor,
                         const uint8_t *__restrict__ refmask, uint8_t *fused)
 {
@@ -559,7 +626,22 @@ static amr_status build_tree(const amr_geom *geom, const int32_t *h_lxyz, const 
     for (int f = 0; f < 6; ++f) bv.bc[f] = geom->bc[f];
     for (int l = 0; l < AMR_MAXLEV + 2; ++l) bv.lvl_off[l] = out->lvl_off[l];
     bv.lvl = out->lvl; bv.ix = out->ix; bv.iy = out->iy; bv.iz = out->iz; bv.key = out->key;
-    k_tables<<<nb, TB, 0, st>>>(bv, out->son, out->father, out->nbor, out->nb27, out->refmask, err);
+    // son and father for every oct, the other tables of levels 1-2 by search, then level by
+    // level from the coarser tables
+    AMR_CUDA_TRY(cudaMemsetAsync(out->son, 0xFF, 32 * size_t(n), st));
+    k_father_son<<<nb, TB, 0, st>>>(bv, out->son, out->father, err);
+    {
+        const int64_t o12 = out->lvl_off[3 <= AMR_MAXLEV + 1 ? 3 : AMR_MAXLEV + 1];
+        if (o12 > 0)
+            k_tables<<<unsigned((o12 + TB - 1) / TB), TB, 0, st>>>(bv, o12, out->son, out->father, out->nbor,
+                                                                    out->nb27, out->refmask, err);
+        for (int l = 3; l <= lmax; ++l) {
+            const int64_t nl = out->lvl_off[l + 1] - out->lvl_off[l];
+            if (nl > 0)
+                k_tables_level<<<unsigned((nl + TB - 1) / TB), TB, 0, st>>>(bv, l, out->son, out->father, out->nbor,
+                                                                         out->nb27, out->refmask, err);
+        }
+    }
     k_fused<<<nb, TB, 0, st>>>(bv, out->son, out->nbor, out->refmask, out->fused);
     {
         // the deepest complete level (levelmin at least): its oct grid for the z-column kernel

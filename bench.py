@@ -228,7 +228,22 @@ def time_e2e(H, tree, prm, w0, steps, stream):
     t1.synchronize()
     ms = t0.elapsed_time(t1) / steps
     nbytes = sim.u.numel() * 8
-    return ms, nbytes
+    # the copies alone, in and out concurrently on two streams: the floor this pipeline
+    # approaches (the host link, not the kernel, bounds the end-to-end step)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    c0.record(s_in)
+    s_out.wait_event(c0)
+    for k in range(steps):
+        with torch.cuda.stream(s_in):
+            u_in[k % 2].copy_(host_in, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            host_out[k % 2].copy_(u_out[k % 2], non_blocking=True)
+    s_in.wait_stream(s_out)
+    c1.record(s_in)
+    c1.synchronize()
+    copy_ms = c0.elapsed_time(c1) / steps
+    return ms, nbytes, copy_ms
 
 
 def cpu_baseline(lx, rho, v, sample_steps=1):
@@ -848,9 +863,11 @@ def main():
         out["l1_rho_chosen_vs_fp64"] = l1
         del sim64
     if not args.skip_e2e:
-        ems, nbytes = time_e2e(H, tree, prm32, w0, args.steps, stream)
+        ems, nbytes, copy_ms = time_e2e(H, tree, prm32, w0, args.steps, stream)
         out["e2e"] = {"value": ws * leaf / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                      "d2h_bytes_per_step": nbytes, "ms_per_step": ems}
+                      "d2h_bytes_per_step": nbytes, "ms_per_step": ems,
+                      "copies_only_ms_per_step": copy_ms, "frac_of_copy_floor": copy_ms / ems,
+                      "link_gbs_per_direction": nbytes / (copy_ms * 1e-3) / 1e9}
     if rank == 0 and ws == 1 and not args.skip_cpu:
         out["cpu_baseline"] = cpu_baseline(lx, rho, v)
     if rank == 0:

@@ -264,7 +264,15 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             zfaces(k + 1, 2);
         };
         // FP64 update of cell q of slab k (fused CFL candidate); keeps the new state
-        auto update = [&](int k, int q) {
+        // the old state of cell q of slab k, loaded ahead of the update
+        auto update_load = [&](int k, int q, double Uo[NV]) -> int32_t {
+            const int dz = q / (FX * FY), r = q % (FX * FY), x = r % FX, y = r / FX;
+            const int32_t cid = cell_id(X0 + 2 + x, Y0 + 2 + y, k + dz);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Uo[v] = uo[v][cid];
+            return cid;
+        };
+        auto update = [&](int k, int q, const double Uo[NV], int32_t cid) {
             const int dz = q / (FX * FY), r = q % (FX * FY), x = r % FX, y = r / FX;
             const int p = k + dz;
             const int ub = (k >> 1) & 1;
@@ -290,12 +298,11 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 if (!sk[5]) dU[v] = dU[v] - sm.Fz[fzu][v][r];
             }
             const bool nbref = sk[0] || sk[1] || sk[2] || sk[3] || sk[4] || sk[5];
-            const int32_t cid = cell_id(X0 + 2 + x, Y0 + 2 + y, p);
             double Un[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                if (sizeof(R) == 8) Un[v] = uo[v][cid] + lam * to_state(dU[v]);
-                else Un[v] = uo[v][cid] + to_state(lamR * dU[v]);
+                if (sizeof(R) == 8) Un[v] = Uo[v] + lam * to_state(dU[v]);
+                else Un[v] = Uo[v] + to_state(lamR * dU[v]);
                 un[v][cid] = Un[v];
                 sm.U[ub][v][q] = Un[v];
             }
@@ -337,12 +344,19 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         __syncthreads();
         // per slab k: {update of slab k, gather of the layer slab k+2 needs, restriction of
         // slab k-2} share one phase, then the predictions and faces of slab k+2
+        static_assert(NU <= 256, "one update item per thread of a 256-thread CTA");
         for (int k = z0; k < z0 + a.zc; k += 2) {
             const bool more = k + 2 < z0 + a.zc;
             const int nwork = NU + (more ? NG : 0) + (k > z0 ? NR : 0);
-            for (int w = tid; w < nwork; w += nt) {
+            // a thread with an update item loads its old state first, so that the load
+            // latency overlaps its gather or restriction item; the update follows them
+            const bool upd = tid < NU;
+            double Uo[NV];
+            int32_t ucid = 0;
+            if (upd) ucid = update_load(k, tid, Uo);
+            for (int w = upd ? tid + nt : tid; w < nwork; w += nt) {
                 if (w < NU) {
-                    update(k, w);
+                    // not reached: update items are the threads' first items
                 } else if (more && w < NU + NG) {
                     const int q = w - NU, o = q >> 3, c = q & 7;
                     const int i = 2 * (o % (SX / 2)) + (c & 1), j = 2 * (o / (SX / 2)) + ((c >> 1) & 1);
@@ -359,6 +373,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                     if (!batch) restrict_one(k - 2, w - NU - (more ? NG : 0));
                 }
             }
+            if (upd) update(k, tid, Uo, ucid);
             __syncthreads();
             if (!more) break;
             predict(k + 3);

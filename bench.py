@@ -97,6 +97,22 @@ def dist_setup():
     return ws, rank, local
 
 
+def job_ms(ms, ws, device):
+    """Whole-job time of a step: the slowest rank's (every rank runs its own box)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, ws, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return ws * units_per_rank / (ms * 1e-3)
+
+
 def make_workload():
     import numpy as np
     from paper_2411_14631_gb300 import workloads as W
@@ -823,11 +839,8 @@ def main():
     ms, sim32 = time_graph(H, tree, prm32, w0, args.steps, args.warmup)
     barrier()
     clocks = clk.stop()
-    if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = ws * leaf / (ms * 1e-3)
+    ms = job_ms(ms, ws, dev)
+    value = job_value(leaf, ws, ms)
     status, counters = prm32.read_status()
 
     hbm, peak_kind = peaks()

@@ -772,6 +772,7 @@ def leaf_count(tree):
 
 
 def main():
+    global LEVEL, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -782,6 +783,8 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--study", default=None, choices=["surrogate", "sedov", "amr", "poisson"])
+    ap.add_argument("--level", type=int, default=8,
+                    help="level of the turbulent box (2^level cells per axis); 8 is the benchmark's 256^3")
     ap.add_argument("--poisson-n", type=int, default=256)
     ap.add_argument("--poisson-tile-y", type=int, default=0, help="8 or 16; 0 tries both")
     ap.add_argument("--poisson-seg", type=int, default=-1, help="z planes per block; -1 tries several")
@@ -789,6 +792,10 @@ def main():
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--tol", type=float, default=0.02)
     args = ap.parse_args()
+    if args.level != LEVEL:
+        n = 1 << args.level
+        WORKLOAD = WORKLOAD.replace("256^3", "%d^3" % n).replace("levels 1-8", "levels 1-%d" % args.level)
+        LEVEL = args.level
     ws, rank, local = dist_setup()
     if args.study == "surrogate":
         return study_surrogate(args)

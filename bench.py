@@ -494,35 +494,6 @@ def study_sedov(args):
         res[name] = {"ms_per_step": ms, "cell_updates_per_s": cells / (ms * 1e-3), "steps_timed": steps}
     res["speedup"] = res["fp64_plain"]["ms_per_step"] / res["fp32_chosen"]["ms_per_step"]
     out["throughput"] = res
-    # sub-cycled levels (level l makes 2^(l-7) steps per coarse step): simulated time per
-    # wall-clock second against one time step for all levels, FP32 path, CUDA graphs
-    prm32 = H.Params(5.0 / 3.0, cfl=CFL, precision=abi.PREC_FP32, tile=tile)
-    single = H.Simulation(tree, prm32, w0=w0)
-    dt_single = float(single.dt.item())
-    del single
-    sc = H.SubcycledSimulation(tree, prm32, w0=w0).use_graph()
-    for _ in range(2):
-        sc.step()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nsc = max(3, args.steps // 2)
-    e0.record()
-    for _ in range(nsc):
-        sc.step()
-    e1.record()
-    torch.cuda.synchronize()
-    ms_sc = e0.elapsed_time(e1) / nsc
-    dt_sc = float(sc.dt.item())
-    per_level = {int(l): int((leaf & (lvl == l)).sum()) for l in range(7, 13)}
-    upd = sum(n * 2 ** (l - 7) for l, n in per_level.items())
-    out["subcycled"] = {"ms_per_coarse_step": ms_sc, "dt_coarse": dt_sc, "dt_single_level_step": dt_single,
-                        "leaf_updates_per_coarse_step": upd, "leaf_updates_per_s": upd / (ms_sc * 1e-3),
-                        "sim_time_per_wall_s": dt_sc / (ms_sc * 1e-3),
-                        "sim_time_per_wall_s_single_dt": dt_single / (res["fp32_chosen"]["ms_per_step"] * 1e-3),
-                        "steps_timed": nsc}
-    out["subcycled"]["gain_in_sim_time_per_wall_s"] = (out["subcycled"]["sim_time_per_wall_s"] /
-                                                       out["subcycled"]["sim_time_per_wall_s_single_dt"])
-    del sc
     out["tile_depth"] = tile
     out["autotune_ms_per_step"] = tune_ms
     # accuracy run: FP32 chosen path, each box frozen at its own target radius

@@ -119,7 +119,9 @@ typedef struct {
                                                hydro_godunov_level (all eight cells leaves, none next
                                                to a refined cell), 0 if hydro_reflux_level does it */
     int32_t *tile_root[2];                  /* per tile: root oct (level l-d-1); batch mode: corner oct */
-    int32_t *tile_slot[2];                  /* per tile: (2^(d+1)+2)^3 stencil slots */
+    int32_t *tile_slot[2];                  /* per tile: (2^(d+1)+2)^3 stencil slots: an oct (>= 0), a
+                                               ghost father -(1+g), INT32_MIN beyond an outflow face,
+                                               or INT32_MIN+1 (not needed) */
     /* batch mode (n_inst > 0): octs of box i are [inst_oct_off[i], inst_oct_off[i+1]) in
        lexicographic (ix fastest) order, lvl[oct] holds the box index, no refinement; the
        time step is per box: d_dt and d_dt_next of the hydro calls are arrays [n_inst]. */
@@ -137,6 +139,13 @@ typedef struct {
        col_work = 0 if not available */
     int64_t col_work;
     int64_t *inst_col_off;
+    /* octree mode: the coarse leaves that tiles interpolate from (ghost fathers), in cell
+       order; a tile slot -(1+g) (g >= 0) stands for the children of cell ghost_cell[g];
+       the ghost fathers of level l are [ghost_off[l], ghost_off[l+1]).  Their interpolated
+       children are computed once per update call into the flux-register buffer. */
+    int64_t n_ghost;
+    int64_t ghost_off[AMR_MAXLEV + 2];
+    int32_t *ghost_cell;
 } amr_tree;
 
 /* Sizes of the caller buffers amr_build_octree needs for this oct list (host list of
@@ -211,8 +220,9 @@ amr_status hydro_step(const amr_tree *tree, const hydro_params *params, const do
    and hosts whose device memory is owned by another framework's memory pool.  For them,
    the flux register lives in a fixed array inside this library, sized for at most
    AMR_STATIC_REG_MAX_OCTS octs above levelmin (31.5 MB, held by every GPU that loads
-   the library until the process exits).  Trees with more such octs get AMR_ECAPACITY and
-   nothing runs.  Inputs and outputs are the caller's, as for hydro_step.  The first
+   the library until the process exits).  Trees with more such octs, or whose register
+   with its ghost-children part (hydro_flux_reg_bytes) exceeds the array, get
+   AMR_ECAPACITY and nothing runs.  Inputs and outputs are the caller's, as for hydro_step.  The first
    call on each device looks up the array's device address (no allocation); make that
    first call before any stream capture.  Every call shares the one array: calls whose
    work overlaps on the GPU (other streams, other host threads) race and give wrong

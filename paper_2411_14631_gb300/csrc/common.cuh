@@ -114,10 +114,24 @@ struct TreeView {
     const uint8_t *refmask, *fused;
     const uint64_t *key;                 // Hilbert keys (octs sorted by level, then key)
     const int32_t *nb27;                 // same-level neighbour octs (refinement)
+    const int32_t *ghost_cell;           // coarse leaves the tiles interpolate from
     int32_t n_inst;                      // batch mode: number of boxes (0: octree)
     const int32_t *inst_n;
     const double *inst_dx;
 };
+
+// The flux-register buffer: rows [oct - reg_base][6 faces][NV] of FP64, then (256-byte
+// aligned) the interpolated children of the ghost fathers, [n_ghost][8][NV] values of the
+// working precision (room for FP64).
+inline size_t reg_rows_bytes(const amr_tree *t)
+{
+    const int64_t rows = t->noct - t->reg_base;
+    return (size_t(rows > 0 ? rows : 1) * 6 * NV * sizeof(double) + 255) & ~size_t(255);
+}
+inline size_t reg_total_bytes(const amr_tree *t)
+{
+    return reg_rows_bytes(t) + size_t(t->n_ghost > 0 ? t->n_ghost : 0) * 8 * NV * sizeof(double);
+}
 
 inline TreeView make_view(const amr_tree *t)
 {
@@ -131,7 +145,7 @@ inline TreeView make_view(const amr_tree *t)
     v.reg_base = t->reg_base;
     v.lvl = t->lvl; v.ix = t->ix; v.iy = t->iy; v.iz = t->iz;
     v.son = t->son; v.nbor = t->nbor; v.father = t->father; v.refmask = t->refmask; v.fused = t->fused;
-    v.key = t->key; v.nb27 = t->nb27;
+    v.key = t->key; v.nb27 = t->nb27; v.ghost_cell = t->ghost_cell;
     v.n_inst = t->n_inst; v.inst_n = t->inst_n; v.inst_dx = t->inst_dx;
     return v;
 }

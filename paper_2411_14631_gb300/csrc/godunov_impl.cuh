@@ -51,6 +51,8 @@ struct GArgs {
     float mlp_tol;            // residual acceptance threshold
     int32_t mlp_seed;         // 1: the network's p* seeds Newton at every face (no acceptance test)
     int32_t limiter;          // AMR_LIMITER_* of the slopes
+    const void *ghost;        // if set: interpolated children of the ghost fathers, R [NV][ghost_stride]
+    int64_t ghost_stride;     // 8 * n_ghost
     double *harvest;          // if set: sampled face states [cap][6] are written, u_new is not
     int64_t harvest_cap, harvest_stride;
     unsigned long long *harvest_count;
@@ -103,6 +105,20 @@ __device__ void interp_child(const TreeView &tv, const double *__restrict__ u, i
         }
         out[v] = r;
     }
+}
+
+// The children of ghost fathers [g0, g1), all eight per father, into out[v][8 g + c]: the
+// values the tiles of the next finer level read in place of absent octs.
+template <typename R>
+__global__ void __launch_bounds__(256) k_ghost(TreeView tv, const double *__restrict__ u, int64_t g0, int64_t g1,
+                                               int64_t stride, R *__restrict__ out)
+{
+    const int64_t i = 8 * g0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= 8 * g1) return;
+    R Uw[NV];
+    interp_child<R>(tv, u, tv.ghost_cell[i >> 3], int(i & 7), Uw);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * stride + i] = Uw[v];
 }
 
 // cons -> prim from conserved values already in the working precision
@@ -395,8 +411,12 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
                 for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(a.u_old[v * tv.ncell + int64_t(e) * 8 + c]);
             } else if (e == UNNEEDED_SLOT) {
                 Uw[0] = R(1); Uw[1] = R(0); Uw[2] = R(0); Uw[3] = R(0); Uw[4] = R(1);
+            } else if (a.ghost) {
+                const R *gh = static_cast<const R *>(a.ghost) + (int64_t(-1) - e) * 8 + c;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) Uw[v] = gh[v * a.ghost_stride];
             } else {
-                interp_child<R>(tv, a.u_old, int64_t(-1) - e, c, Uw);
+                interp_child<R>(tv, a.u_old, tv.ghost_cell[int64_t(-1) - e], c, Uw);
             }
             R Wc[NV];
             cons_to_prim_w(Uw, pr, Wc);
@@ -636,6 +656,7 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
         a.mlp = p->mlp_weights; a.mlp_tol = p->mlp_resid_tol; a.mlp_seed = p->riemann == AMR_RIEMANN_MLP_SEEDED;
         a.limiter = p->limiter;
         a.harvest = nullptr; a.harvest_cap = 0; a.harvest_stride = 1; a.harvest_count = nullptr;
+        a.ghost = nullptr; a.ghost_stride = 0;
         const int64_t nt = a.t_end;
         constexpr int D2 = 2 - (sizeof(R) == 8);
         if (mlp_like) {
@@ -669,6 +690,19 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
         if (gl < l1) return dispatch_impl<R>(t, -2 - (l1 << 8 | (gl + 1)), &q, u_old, u_new, reg, dt, dt_next, st);
         return AMR_OK;
     }
+    // the children of every coarse leaf these tiles interpolate from, once, into the part
+    // of the flux-register buffer after its rows
+    const void *ghost = nullptr;
+    if (reg && t->n_ghost > 0 && t->ghost_cell) {
+        const int64_t g0 = t->ghost_off[l0 - 1], g1 = t->ghost_off[l1];
+        R *gb = reinterpret_cast<R *>(reinterpret_cast<char *>(reg) + reg_rows_bytes(t));
+        if (g1 > g0) {
+            const int64_t nthr = 8 * (g1 - g0);
+            k_ghost<R><<<unsigned((nthr + 255) / 256), 256, 0, st>>>(make_view(t), u_old, g0, g1, 8 * t->n_ghost, gb);
+            AMR_CUDA_TRY(cudaGetLastError());
+        }
+        ghost = gb;
+    }
     int lsplit = l0;
     while (lsplit <= l1 && lsplit - depth < 1) ++lsplit;
     for (int pass = 0; pass < 2; ++pass) {
@@ -697,6 +731,8 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
         a.harvest_cap = 0;
         a.harvest_stride = 1;
         a.harvest_count = nullptr;
+        a.ghost = ghost;
+        a.ghost_stride = 8 * t->n_ghost;
         constexpr int D2 = 2 - (sizeof(R) == 8);
         amr_status r;
         if (mlp_like) {
@@ -740,6 +776,7 @@ inline amr_status harvest_impl(const amr_tree *t, const hydro_params *p, const d
     a.status = p->d_status; a.counters = nullptr;
     a.mlp = nullptr; a.mlp_tol = 0.0f; a.mlp_seed = 0; a.limiter = p->limiter;
     a.harvest = out; a.harvest_cap = cap; a.harvest_stride = stride; a.harvest_count = count;
+    a.ghost = nullptr; a.ghost_stride = 0;
     return launch<double, 1, AMR_RIEMANN_HLLC>(a, a.t_end - a.t_begin, st);
 }
 

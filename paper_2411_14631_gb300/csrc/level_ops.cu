@@ -212,8 +212,7 @@ using namespace amr;
 extern "C" size_t hydro_flux_reg_bytes(const amr_tree *t)
 {
     if (!t) return 0;
-    const int64_t rows = t->noct - t->reg_base;
-    return size_t(rows > 0 ? rows : 1) * 6 * NV * sizeof(double);
+    return reg_total_bytes(t);
 }
 
 extern "C" amr_status hydro_init_from_prim(const amr_tree *t, const hydro_params *p, const double *d_w, double *d_u,
@@ -387,7 +386,9 @@ extern "C" amr_status hydro_step_static_scratch(const amr_tree *t, const hydro_p
                                                 amr_stream stream)
 {
     if (check(t, p) != AMR_OK || !d_u_old || !d_u_new || !d_dt) return AMR_EINVAL;
-    if (t->noct - t->reg_base > AMR_STATIC_REG_MAX_OCTS) return AMR_ECAPACITY;
+    if (t->noct - t->reg_base > AMR_STATIC_REG_MAX_OCTS ||
+        reg_total_bytes(t) > size_t(AMR_STATIC_REG_MAX_OCTS) * 6 * NV * sizeof(double))
+        return AMR_ECAPACITY;
     int dev = 0;
     AMR_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 256) return AMR_EINVAL;

@@ -15,7 +15,7 @@ constexpr int32_t UNNEEDED = INT32_MIN + 1;
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct TreeLayout {
-    size_t lvl, ix, iy, iz, key, son, father, nbor, nb27, refmask, fused, grid, root[2], slot[2], total;
+    size_t lvl, ix, iy, iz, key, son, father, nbor, nb27, refmask, fused, grid, root[2], slot[2], ghost, total;
     int64_t tile_bound[2];
 };
 
@@ -45,19 +45,24 @@ static TreeLayout tree_layout(int64_t n, const int64_t cnt[AMR_MAXLEV + 2], int 
         L.root[d] = put(4 * L.tile_bound[d]);
         L.slot[d] = put(4 * L.tile_bound[d] * nslot(d + 1));
     }
+    // ghost fathers: coarse leaves of levels levelmin..lmax-1 at most
+    int64_t coarse = 0;
+    for (int l = levelmin; l < lmax; ++l) coarse += 8 * cnt[l];
+    L.ghost = put(4 * (coarse > 0 ? coarse : 1));
     L.total = o;
     return L;
 }
 
-struct WsLayout { size_t lxyz, sk0, sk1, id0, id1, flag, pos, small, cub, total; size_t cub_bytes; };
+struct WsLayout { size_t lxyz, sk0, sk1, id0, id1, flag, pos, gflag, gpos, small, cub, total; size_t cub_bytes; };
 
 static size_t cub_bytes_needed(int64_t n)
 {
-    size_t a = 0, b = 0;
+    size_t a = 0, b = 0, c = 0;
     cub::DeviceRadixSort::SortPairs(nullptr, a, (uint64_t *)nullptr, (uint64_t *)nullptr, (int32_t *)nullptr,
                                     (int32_t *)nullptr, (int)n, 0, 64);
     cub::DeviceScan::ExclusiveSum(nullptr, b, (int32_t *)nullptr, (int32_t *)nullptr, (int)n);
-    return a > b ? a : b;
+    cub::DeviceScan::ExclusiveSum(nullptr, c, (int32_t *)nullptr, (int32_t *)nullptr, (int)(8 * n + 1));
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
 }
 
 static WsLayout ws_layout(int64_t n)
@@ -66,7 +71,9 @@ static WsLayout ws_layout(int64_t n)
     size_t o = 0;
     auto put = [&](size_t bytes) { size_t at = o; o += al256(bytes); return at; };
     W.lxyz = put(16 * n); W.sk0 = put(8 * n); W.sk1 = put(8 * n); W.id0 = put(4 * n); W.id1 = put(4 * n);
-    W.flag = put(4 * (n + 1)); W.pos = put(4 * (n + 1)); W.small = put(2048);   // err, tile counts, level histogram
+    W.flag = put(4 * (n + 1)); W.pos = put(4 * (n + 1));
+    W.gflag = put(4 * (8 * n + 1)); W.gpos = put(4 * (8 * n + 1));   // ghost fathers, per cell
+    W.small = put(2048);   // err, tile counts, level histogram, ghost offsets
     W.cub_bytes = cub_bytes_needed(n);
     W.cub = put(W.cub_bytes);
     W.total = o;
@@ -370,6 +377,37 @@ __global__ void k_tile_slots(BuildView b, int depth, int64_t ntile, const int32_
         else v = son[F] >= 0 ? son[F] : int32_t(-1 - F);
     }
     slot[gi] = v;
+}
+
+// Ghost fathers: every coarse leaf a tile slot interpolates from gets one index, in cell
+// order; the slots are rewritten to refer to that index.
+__global__ void k_ghost_mark(int64_t nslots, const int32_t *__restrict__ slot, int32_t *gflag)
+{
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= nslots) return;
+    const int32_t v = slot[i];
+    if (v < 0 && v != OUTSIDE && v != UNNEEDED) gflag[-1 - int64_t(v)] = 1;
+}
+
+__global__ void k_ghost_compact(int64_t ncell, const int32_t *__restrict__ gflag, const int32_t *__restrict__ gpos,
+                                int32_t *ghost_cell)
+{
+    const int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (c < ncell && gflag[c]) ghost_cell[gpos[c]] = int32_t(c);
+}
+
+__global__ void k_ghost_rewrite(int64_t nslots, const int32_t *__restrict__ gpos, int32_t *slot)
+{
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= nslots) return;
+    const int32_t v = slot[i];
+    if (v < 0 && v != OUTSIDE && v != UNNEEDED) slot[i] = -1 - gpos[-1 - int64_t(v)];
+}
+
+__global__ void k_ghost_bounds(BuildView b, const int32_t *__restrict__ gpos, int64_t *out)
+{
+    const int l = threadIdx.x;
+    if (l < AMR_MAXLEV + 2) out[l] = gpos[b.lvl_off[l] * 8];
 }
 
 // ---- batch mode: independent uniform boxes -------------------------------------------
@@ -679,10 +717,35 @@ static amr_status build_tree(const amr_geom *geom, const int32_t *h_lxyz, const 
                                                                       out->tile_slot[d]);
         }
     }
+    // ghost fathers: one index per coarse leaf the tiles interpolate from, in cell order
+    {
+        const int64_t ncell = 8 * n;
+        int32_t *gflag = (int32_t *)(S + W.gflag), *gpos = (int32_t *)(S + W.gpos);
+        int64_t *goff = (int64_t *)(S + W.small + 1280);
+        out->ghost_cell = (int32_t *)(T + L.ghost);
+        AMR_CUDA_TRY(cudaMemsetAsync(gflag, 0, 4 * size_t(ncell + 1), st));
+        for (int d = 0; d < 2; ++d) {
+            const int64_t ns = out->tile_off[d][AMR_MAXLEV + 1] * nslot(d + 1);
+            if (ns > 0) k_ghost_mark<<<unsigned((ns + TB - 1) / TB), TB, 0, st>>>(ns, out->tile_slot[d], gflag);
+        }
+        cb = W.cub_bytes;
+        AMR_CUDA_TRY(cub::DeviceScan::ExclusiveSum(cubtmp, cb, gflag, gpos, (int)(ncell + 1), st));
+        k_ghost_compact<<<unsigned((ncell + TB - 1) / TB), TB, 0, st>>>(ncell, gflag, gpos, out->ghost_cell);
+        for (int d = 0; d < 2; ++d) {
+            const int64_t ns = out->tile_off[d][AMR_MAXLEV + 1] * nslot(d + 1);
+            if (ns > 0) k_ghost_rewrite<<<unsigned((ns + TB - 1) / TB), TB, 0, st>>>(ns, gpos, out->tile_slot[d]);
+        }
+        k_ghost_bounds<<<1, 32, 0, st>>>(bv, gpos, goff);
+        AMR_CUDA_TRY(cudaMemcpyAsync(out->ghost_off, goff, sizeof(out->ghost_off), cudaMemcpyDeviceToHost, st));
+    }
     AMR_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, st));
     AMR_CUDA_TRY(cudaStreamSynchronize(st));
     AMR_CUDA_TRY(cudaGetLastError());
     if (herr != 0) return amr_status(herr);
+    out->n_ghost = out->ghost_off[AMR_MAXLEV + 1];
+    int64_t coarse = 0;
+    for (int l = lmin; l < lmax; ++l) coarse += 8 * cnt[l];
+    if (out->n_ghost > (coarse > 0 ? coarse : 1)) return AMR_ECAPACITY;   // cannot happen for a valid tree
     return AMR_OK;
 }
 

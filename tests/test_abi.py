@@ -49,12 +49,13 @@ def test_struct_layout_matches_c(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "amrhydro.h"\n'
                    'int main(){printf("%zu %zu %zu %zu %zu\\n", sizeof(amr_tree), sizeof(hydro_params),'
-                   ' sizeof(amr_geom), offsetof(amr_tree, tile_slot), offsetof(hydro_params, d_counters));}\n')
+                   ' sizeof(amr_geom), offsetof(amr_tree, tile_slot), offsetof(hydro_params, d_counters));'
+                   ' printf("%zu\\n", offsetof(amr_tree, ghost_cell));}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert got == [C.sizeof(abi.AmrTree), C.sizeof(abi.HydroParams), C.sizeof(abi.AmrGeom),
-                   abi.AmrTree.tile_slot.offset, abi.HydroParams.d_counters.offset]
+                   abi.AmrTree.tile_slot.offset, abi.HydroParams.d_counters.offset, abi.AmrTree.ghost_cell.offset]
 
 
 def test_query_is_host_only_and_validates(built):

@@ -192,10 +192,12 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             }
         };
         auto q3 = [](int p) { return (p + 6) % 3; };   // planes start at z0 - 2 >= -2
-        // MinMod slopes + MUSCL-Hancock predictor of plane p (cells 1..SX-2 x 1..SY-2)
-        auto predict = [&](int p) {
-            const int s0 = p & 3, sm1 = (p - 1) & 3, sp1 = (p + 1) & 3, qs = q3(p);
-            for (int r = tid; r < PX * PY; r += nt) {
+        // MinMod slopes + MUSCL-Hancock predictor of planes p0 and p0+1 (cells 1..SX-2 x
+        // 1..SY-2 of each), one loop so that every warp of the CTA takes a share
+        auto predict2 = [&](int p0) {
+            for (int r2 = tid; r2 < 2 * PX * PY; r2 += nt) {
+                const int dp = r2 >= PX * PY, r = r2 - dp * (PX * PY), p = p0 + dp;
+                const int s0 = p & 3, sm1 = (p - 1) & 3, sp1 = (p + 1) & 3, qs = q3(p);
                 const int i = 1 + r % PX, j = 1 + r / PX;
                 const int si = i + SX * j;
                 R Wc[NV], Dl[3][NV];
@@ -239,29 +241,41 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
 
         constexpr int NXF = FY * (FX + 1), NYF = (FY + 1) * FX;
         constexpr int NG = (SX / 2) * (SY / 2) * 8, NU = 2 * FX * FY, NR = (FX / 2) * (FY / 2) * NV;
-        // x and y faces of planes k, k+1 and z faces below planes k+1, k+2 (those of slab k)
+        // x and y faces of planes k, k+1 and z faces below planes k+1, k+2 (those of slab k),
+        // one loop over all three kinds: the face states are formed per kind, the Riemann
+        // solve is shared (a warp that straddles two kinds solves once), the flux is stored
+        // per kind
         auto slab_faces = [&](int k) {
-            const int qk0 = q3(k), qk1 = q3(k + 1);
-            for (int r = tid; r < 2 * (NXF + NYF); r += nt) {
+            const int qk0 = q3(k), qk1 = q3(k + 1), qk2 = q3(k + 2);
+            for (int r = tid; r < 2 * (NXF + NYF + FX * FY); r += nt) {
                 R WL[NV], WR[NV], Fn[NV];
+                int kind, dz, rr;
                 if (r < 2 * NXF) {
-                    const int dz = r / NXF, rr = r % NXF, fa = rr % (FX + 1), row = rr / (FX + 1);
+                    kind = 0; dz = r / NXF; rr = r % NXF;
+                    const int fa = rr % (FX + 1), row = rr / (FX + 1);
                     const int pl = fa + PX * (1 + row);
                     const int qs = dz ? qk1 : qk0;
                     col_face<R, 0, PX * PY>(sm.Q[qs], sm.Q[qs], pl, pl + 1, pr, WL, WR);
-                    col_solve<R, RS>(WL, WR, pr, a.status, Fn);
-                    col_store<0>(sm.Fx[dz], rr, Fn);
-                } else {
+                } else if (r < 2 * (NXF + NYF)) {
                     const int r2 = r - 2 * NXF;
-                    const int dz = r2 / NYF, rr = r2 % NYF, col = rr % FX, fa = rr / FX;
+                    kind = 1; dz = r2 / NYF; rr = r2 % NYF;
+                    const int col = rr % FX, fa = rr / FX;
                     const int pl = (1 + col) + PX * fa;
                     const int qs = dz ? qk1 : qk0;
                     col_face<R, 1, PX * PY>(sm.Q[qs], sm.Q[qs], pl, pl + PX, pr, WL, WR);
-                    col_solve<R, RS>(WL, WR, pr, a.status, Fn);
-                    col_store<1>(sm.Fy[dz], rr, Fn);
+                } else {
+                    // the face below plane k+1+dz: between planes k+dz and k+1+dz
+                    const int r2 = r - 2 * (NXF + NYF);
+                    kind = 2; dz = r2 / (FX * FY); rr = r2 % (FX * FY);
+                    const int x = rr % FX, y = rr / FX;
+                    const int pq = (1 + x) + PX * (1 + y);
+                    col_face<R, 2, PX * PY>(sm.Q[dz ? qk1 : qk0], sm.Q[dz ? qk2 : qk1], pq, pq, pr, WL, WR);
                 }
+                col_solve<R, RS>(WL, WR, pr, a.status, Fn);
+                if (kind == 0) col_store<0>(sm.Fx[dz], rr, Fn);
+                else if (kind == 1) col_store<1>(sm.Fy[dz], rr, Fn);
+                else col_store<2>(sm.Fz[dz ? qk2 : qk1], rr, Fn);
             }
-            zfaces(k + 1, 2);
         };
         // FP64 update of cell q of slab k (fused CFL candidate); keeps the new state
         // the old state of cell q of slab k, loaded ahead of the update
@@ -331,14 +345,12 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         gather(z0 / 2 - 1);
         gather(z0 / 2);
         __syncthreads();
-        predict(z0 - 1);
-        predict(z0);
+        predict2(z0 - 1);
         __syncthreads();
         zfaces(z0, 1);
         gather(z0 / 2 + 1);
         __syncthreads();
-        predict(z0 + 1);
-        predict(z0 + 2);
+        predict2(z0 + 1);
         __syncthreads();
         slab_faces(z0);
         __syncthreads();
@@ -376,8 +388,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             if (upd) update(k, tid, Uo, ucid);
             __syncthreads();
             if (!more) break;
-            predict(k + 3);
-            predict(k + 4);
+            predict2(k + 3);
             __syncthreads();
             slab_faces(k + 2);
             __syncthreads();

@@ -26,6 +26,7 @@ template <typename R, int FX, int FY, bool FINER> struct ColSmem {
     R Fz[3][NV][FY * FX];                            // face below plane j, slot (j + 6) % 3
     double U[2][NV][2 * FY * FX];                    // new states of the last two slabs
     int32_t cell[2][2 * FY * FX];                    // their cell ids (oct*8 + c)
+    int32_t oct[4][(SX / 2) * (SY / 2)];             // oct id per footprint oct column, slot = oct layer & 3
     // refined flag of each stencil cell, slot = plane & 7 (live: k-1 .. k+5, longer than the
     // W ring); only when the level has finer levels (keeps 4 CTAs per SM otherwise)
     uint8_t ref[FINER ? 8 : 1][FINER ? SY * SX : 1];
@@ -168,33 +169,48 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             return c < 0 ? 0 : ni - 1;             // outflow: clamp at this level
         };
         const int32_t Mi = int32_t(M);
-        auto cell_id = [&](int x, int y, int z) -> int32_t {
-            const int32_t oi = (x >> 1) + Mi * ((y >> 1) + Mi * (z >> 1));
-            const int32_t o = batch ? obase + oi : a.grid[oi];
-            return o * 8 + (x & 1) + 2 * (y & 1) + 4 * (z & 1);
-        };
 
-        // gather oct layer L (cell planes 2L, 2L+1) of the stencil footprint into the W ring
+        // the oct ids of the footprint's oct columns at oct layer L, wrapped or clamped like
+        // the cells (X0, Y0 are even, so both cells of a footprint oct slot, and both planes
+        // of a layer, land in one oct)
+        constexpr int NO = (SX / 2) * (SY / 2);
+        auto oct_fill = [&](int L, int o) {
+            const int wx = wrap(X0 + 2 * (o % (SX / 2)), 0), wy = wrap(Y0 + 2 * (o / (SX / 2)), 1);
+            const int32_t oi = (wx >> 1) + Mi * ((wy >> 1) + Mi * (wrap(2 * L, 2) >> 1));
+            sm.oct[L & 3][o] = batch ? obase + oi : a.grid[oi];
+        };
+        // item q of the gather of oct layer L (cell planes 2L, 2L+1) of the stencil footprint
+        // into the W ring
+        auto gather_item = [&](int L, int q) {
+            const int o = q >> 3, c = q & 7;
+            const int i = 2 * (o % (SX / 2)) + (c & 1), j = 2 * (o / (SX / 2)) + ((c >> 1) & 1);
+            const int zp = 2 * L + ((c >> 2) & 1);
+            const int32_t cid = sm.oct[L & 3][o] * 8 + (wrap(X0 + i, 0) & 1) + 2 * (wrap(Y0 + j, 1) & 1) +
+                                4 * (wrap(zp, 2) & 1);
+            R Uw[NV], Wc[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(uo[v][cid]);
+            cons_to_prim_w(Uw, pr, Wc);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sm.W[zp & 3][v][i + SX * j] = Wc[v];
+            if constexpr (FINER) sm.ref[zp & 7][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
+        };
         auto gather = [&](int L) {
-            for (int q = tid; q < (SX / 2) * (SY / 2) * 8; q += nt) {
-                const int o = q >> 3, c = q & 7;
-                const int i = 2 * (o % (SX / 2)) + (c & 1), j = 2 * (o / (SX / 2)) + ((c >> 1) & 1);
-                const int zp = 2 * L + ((c >> 2) & 1);
-                const int32_t cid = cell_id(wrap(X0 + i, 0), wrap(Y0 + j, 1), wrap(zp, 2));
-                R Uw[NV], Wc[NV];
-#pragma unroll
-                for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(uo[v][cid]);
-                cons_to_prim_w(Uw, pr, Wc);
-                const int slot = zp & 3;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) sm.W[slot][v][i + SX * j] = Wc[v];
-                if constexpr (FINER) sm.ref[zp & 7][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
-            }
+            for (int q = tid; q < NO * 8; q += nt) gather_item(L, q);
+        };
+        // L2 prefetch of the oct rows (two 32-byte halves per variable) of oct layer L
+        auto prefetch_item = [&](int L, int w) {
+            const int o = w / (2 * NV), v = (w / 2) % NV, h = w & 1;
+            const double *ptr = a.u_old + int64_t(v) * tv.ncell + int64_t(sm.oct[L & 3][o]) * 8 + 4 * h;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
         };
         auto q3 = [](int p) { return (p + 6) % 3; };   // planes start at z0 - 2 >= -2
         // MinMod slopes + MUSCL-Hancock predictor of planes p0 and p0+1 (cells 1..SX-2 x
         // 1..SY-2 of each), one loop so that every warp of the CTA takes a share
-        auto predict2 = [&](int p0) {
+        auto predict2 = [&](int p0, bool fill, int fillL) {
+            // threads past the predictions fill the oct table of layer fillL
+            if (fill)
+                for (int w = tid - 2 * PX * PY; w >= 0 && w < NO; w += nt) oct_fill(fillL, w);
             for (int r2 = tid; r2 < 2 * PX * PY; r2 += nt) {
                 const int dp = r2 >= PX * PY, r = r2 - dp * (PX * PY), p = p0 + dp;
                 const int s0 = p & 3, sm1 = (p - 1) & 3, sp1 = (p + 1) & 3, qs = q3(p);
@@ -245,9 +261,13 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         // one loop over all three kinds: the face states are formed per kind, the Riemann
         // solve is shared (a warp that straddles two kinds solves once), the flux is stored
         // per kind
-        auto slab_faces = [&](int k) {
+        constexpr int NF = 2 * (NXF + NYF + FX * FY), NP = NO * NV * 2;
+        auto slab_faces = [&](int k, bool pf, int pfL) {
             const int qk0 = q3(k), qk1 = q3(k + 1), qk2 = q3(k + 2);
-            for (int r = tid; r < 2 * (NXF + NYF + FX * FY); r += nt) {
+            // the prefetches of oct layer pfL go out first; nothing waits on them
+            if (pf)
+                for (int w = tid; w < NP; w += nt) prefetch_item(pfL, w);
+            for (int r = tid; r < NF; r += nt) {
                 R WL[NV], WR[NV], Fn[NV];
                 int kind, dz, rr;
                 if (r < 2 * NXF) {
@@ -281,7 +301,8 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         // the old state of cell q of slab k, loaded ahead of the update
         auto update_load = [&](int k, int q, double Uo[NV]) -> int32_t {
             const int dz = q / (FX * FY), r = q % (FX * FY), x = r % FX, y = r / FX;
-            const int32_t cid = cell_id(X0 + 2 + x, Y0 + 2 + y, k + dz);
+            const int o = ((x + 2) >> 1) + (SX / 2) * ((y + 2) >> 1);
+            const int32_t cid = sm.oct[(k >> 1) & 3][o] * 8 + (x & 1) + 2 * (y & 1) + 4 * dz;
 #pragma unroll
             for (int v = 0; v < NV; ++v) Uo[v] = uo[v][cid];
             return cid;
@@ -341,18 +362,20 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         // prologue, keeping to the ring sizes (W: 4 planes, Q and Fz: 3): planes z0-2 .. z0+1,
         // predictions z0-1, z0, the z face below z0 together with planes z0+2, z0+3 (which
         // replace the dead z0-2, z0-1), predictions z0+1, z0+2 (replacing z0-1), the faces
-        // of slab z0
+        // of slab z0; first the oct tables of layers z0/2-1 .. z0/2+2
+        for (int w = tid; w < 4 * NO; w += nt) oct_fill(z0 / 2 - 1 + w / NO, w % NO);
+        __syncthreads();
         gather(z0 / 2 - 1);
         gather(z0 / 2);
         __syncthreads();
-        predict2(z0 - 1);
+        predict2(z0 - 1, false, 0);
         __syncthreads();
         zfaces(z0, 1);
         gather(z0 / 2 + 1);
         __syncthreads();
-        predict2(z0 + 1);
+        predict2(z0 + 1, false, 0);
         __syncthreads();
-        slab_faces(z0);
+        slab_faces(z0, false, 0);
         __syncthreads();
         // per slab k: {update of slab k, gather of the layer slab k+2 needs, restriction of
         // slab k-2} share one phase, then the predictions and faces of slab k+2
@@ -370,17 +393,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 if (w < NU) {
                     // not reached: update items are the threads' first items
                 } else if (more && w < NU + NG) {
-                    const int q = w - NU, o = q >> 3, c = q & 7;
-                    const int i = 2 * (o % (SX / 2)) + (c & 1), j = 2 * (o / (SX / 2)) + ((c >> 1) & 1);
-                    const int zp = k + 4 + ((c >> 2) & 1);
-                    const int32_t cid = cell_id(wrap(X0 + i, 0), wrap(Y0 + j, 1), wrap(zp, 2));
-                    R Uw[NV], Wc[NV];
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(uo[v][cid]);
-                    cons_to_prim_w(Uw, pr, Wc);
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) sm.W[zp & 3][v][i + SX * j] = Wc[v];
-                    if constexpr (FINER) sm.ref[zp & 7][i + SX * j] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
+                    gather_item(k / 2 + 2, w - NU);
                 } else {
                     if (!batch) restrict_one(k - 2, w - NU - (more ? NG : 0));
                 }
@@ -388,9 +401,13 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             if (upd) update(k, tid, Uo, ucid);
             __syncthreads();
             if (!more) break;
-            predict2(k + 3);
+            // the oct table of layer k/2+3 (slot of the dead layer k/2-1), which the gather of
+            // slab k+2 and the update of slab k+6 read, is filled beside the predictions; the
+            // layer's state rows are prefetched into L2 beside the faces
+            const bool ahead = k + 4 < z0 + a.zc;
+            predict2(k + 3, ahead, k / 2 + 3);
             __syncthreads();
-            slab_faces(k + 2);
+            slab_faces(k + 2, ahead, k / 2 + 3);
             __syncthreads();
         }
         // the last slab's restriction

@@ -18,14 +18,26 @@ namespace amr {
 
 template <typename R, int FX, int FY, bool FINER> struct ColSmem {
     static constexpr int SX = FX + 4, SY = FY + 4;   // stencil footprint (cells)
-    static constexpr int PX = FX + 2, PY = FY + 2;   // predicted footprint
     R W[4][NV][SY * SX];                             // ring, slot = plane & 3 (live: k .. k+3)
-    R Q[3][4 * NV][PY * PX];                         // ring, slot = (plane + 6) % 3 (live: k .. k+2)
+    // Q ring, slot = (plane + 6) % 3 (live: k .. k+2).  A plane keeps the predicted cells the
+    // faces read: the FX x FY interior (row-major, stride FX) and four strips outside it,
+    // top (j = FY+2), left (i = 1), bottom (j = 1), right (i = FX+2); the corners are never
+    // read and not kept.  With stride FX an 8 x 4 block of cells is one conflict-free row of
+    // banks; the slot stride is padded by 16 floats (faces whose two sides lie in adjacent
+    // slots, and warps that straddle two planes, then meet fewer bank conflicts).
+    static constexpr int QC = FX * FY + 2 * (FX + FY);
+    static constexpr int QT = FX * FY, QL = QT + FX, QB = QL + FY, QR = QB + FX;
+    static constexpr int QS = 4 * NV * QC + 16;
+    R Q[3][QS];
     R Fx[2][NV][FY * (FX + 1)];                      // x faces of the slab's two planes
     R Fy[2][NV][(FY + 1) * FX];
     R Fz[3][NV][FY * FX];                            // face below plane j, slot (j + 6) % 3
-    double U[2][NV][2 * FY * FX];                    // new states of the last two slabs
-    int32_t cell[2][2 * FY * FX];                    // their cell ids (oct*8 + c)
+    // new states of the last two slabs, [child c][oct o of the slab][variable]; the row
+    // length is padded so that the update's stores (16 lanes: 4 octs x 4 children) and the
+    // restriction's loads (16 lanes: consecutive (oct, variable)) each take one wavefront
+    static constexpr int NOS = (FX / 2) * (FY / 2), UC = NOS * NV + 4;
+    double U[2][8][UC];
+    int32_t cell0[2][NOS];                           // cell id of each oct's child 0 (-1: refined)
     int32_t oct[4][(SX / 2) * (SY / 2)];             // oct id per footprint oct column, slot = oct layer & 3
     // refined flag of each stencil cell, slot = plane & 7 (live: k-1 .. k+5, longer than the
     // W ring); only when the level has finer levels (keeps 4 CTAs per SM otherwise)
@@ -109,9 +121,11 @@ template <typename R, int RS, int FX, int FY, bool FINER>
 __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
 {
     using S = ColSmem<R, FX, FY, FINER>;
-    constexpr int SX = S::SX, SY = S::SY, PX = S::PX, PY = S::PY;
+    constexpr int SX = S::SX, SY = S::SY;
+    constexpr int QC = S::QC, QT = S::QT, QL = S::QL, QB = S::QB, QR = S::QR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
+    auto Qp = [&](int slot) { return reinterpret_cast<R (*)[QC]>(sm.Q[slot]); };
     const TreeView &tv = a.tv;
     const int tid = threadIdx.x, nt = blockDim.x;
     Prm<R> pr;
@@ -210,11 +224,17 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
         auto predict2 = [&](int p0, bool fill, int fillL) {
             // threads past the predictions fill the oct table of layer fillL
             if (fill)
-                for (int w = tid - 2 * PX * PY; w >= 0 && w < NO; w += nt) oct_fill(fillL, w);
-            for (int r2 = tid; r2 < 2 * PX * PY; r2 += nt) {
-                const int dp = r2 >= PX * PY, r = r2 - dp * (PX * PY), p = p0 + dp;
+                for (int w = tid - 2 * QC; w >= 0 && w < NO; w += nt) oct_fill(fillL, w);
+            for (int r2 = tid; r2 < 2 * QC; r2 += nt) {
+                const int dp = r2 >= QC, r = r2 - dp * QC, p = p0 + dp;
                 const int s0 = p & 3, sm1 = (p - 1) & 3, sp1 = (p + 1) & 3, qs = q3(p);
-                const int i = 1 + r % PX, j = 1 + r / PX;
+                // item r is the cell kept at Q index r
+                int i, j;
+                if (r < QT) { i = 2 + r % FX; j = 2 + r / FX; }
+                else if (r < QL) { i = 2 + (r - QT); j = FY + 2; }
+                else if (r < QB) { i = 1; j = 2 + (r - QL); }
+                else if (r < QR) { i = 2 + (r - QB); j = 1; }
+                else { i = FX + 2; j = 2 + (r - QR); }
                 const int si = i + SX * j;
                 R Wc[NV], Dl[3][NV];
 #pragma unroll
@@ -232,13 +252,13 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 Wt[2] = vv - hl * (u * Dl[0][2] + vv * Dl[1][2] + w * Dl[2][2] + Dl[1][4] / rr);
                 Wt[3] = w - hl * (u * Dl[0][3] + vv * Dl[1][3] + w * Dl[2][3] + Dl[2][4] / rr);
                 Wt[4] = pp - hl * (u * Dl[0][4] + vv * Dl[1][4] + w * Dl[2][4] + pr.gamma * pp * (Dl[0][1] + Dl[1][2] + Dl[2][3]));
-                const int pq = (i - 1) + PX * (j - 1);
+                R (*Qs)[QC] = Qp(qs);
 #pragma unroll
-                for (int v = 0; v < NV; ++v) sm.Q[qs][v][pq] = Wt[v];
+                for (int v = 0; v < NV; ++v) Qs[v][r] = Wt[v];
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) sm.Q[qs][NV + NV * d + v][pq] = Dl[d][v];
+                    for (int v = 0; v < NV; ++v) Qs[NV + NV * d + v][r] = Dl[d][v];
             }
         };
         // z faces below planes j (face j-1 | j), for the listed planes
@@ -246,10 +266,9 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             const int qa = q3(j0 - 1), qb = q3(j0), qc = q3(j0 + 1);
             for (int r = tid; r < count * FX * FY; r += nt) {
                 const int dj = r / (FX * FY);          // FX * FY is a power of two
-                const int rr = r % (FX * FY), x = rr % FX, y = rr / FX;
-                const int pq = (1 + x) + PX * (1 + y);
+                const int rr = r % (FX * FY);
                 R WL[NV], WR[NV], Fn[NV];
-                col_face<R, 2, PX * PY>(sm.Q[dj ? qb : qa], sm.Q[dj ? qc : qb], pq, pq, pr, WL, WR);
+                col_face<R, 2, QC>(Qp(dj ? qb : qa), Qp(dj ? qc : qb), rr, rr, pr, WL, WR);
                 col_solve<R, RS>(WL, WR, pr, a.status, Fn);
                 col_store<2>(sm.Fz[dj ? qc : qb], rr, Fn);
             }
@@ -271,25 +290,27 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 R WL[NV], WR[NV], Fn[NV];
                 int kind, dz, rr;
                 if (r < 2 * NXF) {
+                    // x faces, stored at rr: for rr < FX*FY the face on the right of interior
+                    // cell rr, else the face on the left of interior column 0 in row rr - FX*FY
                     kind = 0; dz = r / NXF; rr = r % NXF;
-                    const int fa = rr % (FX + 1), row = rr / (FX + 1);
-                    const int pl = fa + PX * (1 + row);
+                    int pl, pq;
+                    if (rr < QT) { pl = rr; pq = rr % FX == FX - 1 ? QR + rr / FX : rr + 1; }
+                    else { pl = QL + (rr - QT); pq = FX * (rr - QT); }
                     const int qs = dz ? qk1 : qk0;
-                    col_face<R, 0, PX * PY>(sm.Q[qs], sm.Q[qs], pl, pl + 1, pr, WL, WR);
+                    col_face<R, 0, QC>(Qp(qs), Qp(qs), pl, pq, pr, WL, WR);
                 } else if (r < 2 * (NXF + NYF)) {
+                    // y faces, stored at rr = col + FX * fa (fa = 0: below row 0, strip B)
                     const int r2 = r - 2 * NXF;
                     kind = 1; dz = r2 / NYF; rr = r2 % NYF;
                     const int col = rr % FX, fa = rr / FX;
-                    const int pl = (1 + col) + PX * fa;
+                    const int pl = fa == 0 ? QB + col : rr - FX, pq = fa == FY ? QT + col : rr;
                     const int qs = dz ? qk1 : qk0;
-                    col_face<R, 1, PX * PY>(sm.Q[qs], sm.Q[qs], pl, pl + PX, pr, WL, WR);
+                    col_face<R, 1, QC>(Qp(qs), Qp(qs), pl, pq, pr, WL, WR);
                 } else {
                     // the face below plane k+1+dz: between planes k+dz and k+1+dz
                     const int r2 = r - 2 * (NXF + NYF);
                     kind = 2; dz = r2 / (FX * FY); rr = r2 % (FX * FY);
-                    const int x = rr % FX, y = rr / FX;
-                    const int pq = (1 + x) + PX * (1 + y);
-                    col_face<R, 2, PX * PY>(sm.Q[dz ? qk1 : qk0], sm.Q[dz ? qk2 : qk1], pq, pq, pr, WL, WR);
+                    col_face<R, 2, QC>(Qp(dz ? qk1 : qk0), Qp(dz ? qk2 : qk1), rr, rr, pr, WL, WR);
                 }
                 col_solve<R, RS>(WL, WR, pr, a.status, Fn);
                 if (kind == 0) col_store<0>(sm.Fx[dz], rr, Fn);
@@ -314,10 +335,14 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             // with finer levels: a refined cell is left to the restriction, and a face whose
             // other side is refined carries no flux here (the finer level supplies it)
             bool sk[6] = {false, false, false, false, false, false};
+            const int uo8 = (x >> 1) + (FX / 2) * (y >> 1), uc = (x & 1) + 2 * (y & 1) + 4 * dz;
             if constexpr (FINER) {
                 const int si = (x + 2) + SX * (y + 2);
                 const uint8_t *rp = sm.ref[p & 7];
-                if (rp[si]) { sm.cell[ub][q] = -1; return; }
+                if (rp[si]) {
+                    if (uc == 0) sm.cell0[ub][uo8] = -1;
+                    return;
+                }
                 sk[0] = rp[si - 1]; sk[1] = rp[si + 1]; sk[2] = rp[si - SX]; sk[3] = rp[si + SX];
                 sk[4] = sm.ref[(p - 1) & 7][si]; sk[5] = sm.ref[(p + 1) & 7][si];
             }
@@ -325,8 +350,8 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             const int fzl = q3(p), fzu = fzl == 2 ? 0 : fzl + 1;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                if (!sk[0]) dU[v] = dU[v] + sm.Fx[dz][v][x + (FX + 1) * y];
-                if (!sk[1]) dU[v] = dU[v] - sm.Fx[dz][v][x + 1 + (FX + 1) * y];
+                if (!sk[0]) dU[v] = dU[v] + sm.Fx[dz][v][x ? x - 1 + FX * y : FX * FY + y];
+                if (!sk[1]) dU[v] = dU[v] - sm.Fx[dz][v][x + FX * y];
                 if (!sk[2]) dU[v] = dU[v] + sm.Fy[dz][v][x + FX * y];
                 if (!sk[3]) dU[v] = dU[v] - sm.Fy[dz][v][x + FX * (y + 1)];
                 if (!sk[4]) dU[v] = dU[v] + sm.Fz[fzl][v][r];
@@ -339,23 +364,22 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 if (sizeof(R) == 8) Un[v] = Uo[v] + lam * to_state(dU[v]);
                 else Un[v] = Uo[v] + to_state(lamR * dU[v]);
                 un[v][cid] = Un[v];
-                sm.U[ub][v][q] = Un[v];
+                sm.U[ub][uc][uo8 * NV + v] = Un[v];
             }
-            sm.cell[ub][q] = cid;
+            if (uc == 0) sm.cell0[ub][uo8] = cid;
             if (dtn && !nbref) my_dt = min(my_dt, (unsigned long long)__double_as_longlong(cfl_candidate<R>(Un, pr, cflR, dxR)));
         };
         // restriction of the father of one oct of slab k (its eight cells in order), variable v
         auto restrict_one = [&](int k, int w) {
-            const int o = w / NV, v = w % NV, oi = o % (FX / 2), oj = o / (FX / 2);
+            const int o = w / NV, v = w % NV;
             const int ub = (k >> 1) & 1;
-            const int q0 = 2 * oi + FX * (2 * oj);
-            const int32_t c0 = sm.cell[ub][q0];
+            const int32_t c0 = sm.cell0[ub][o];
             if (c0 < 0) return;                       // a refined cell: the oct is not restricted here
             const int32_t oct = c0 >> 3;
             if (!tv.fused[oct]) return;
             double acc = 0.0;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc += sm.U[ub][v][q0 + (c & 1) + FX * ((c >> 1) & 1) + FX * FY * ((c >> 2) & 1)];
+            for (int c = 0; c < 8; ++c) acc += sm.U[ub][c][w];     // w = o * NV + v
             a.u_new[v * tv.ncell + tv.father[oct]] = 0.125 * acc;    // v is not a constant here
         };
 

@@ -22,9 +22,10 @@ template <typename R, int FX, int FY, bool FINER> struct ColSmem {
     // Q ring, slot = (plane + 6) % 3 (live: k .. k+2).  A plane keeps the predicted cells the
     // faces read: the FX x FY interior (row-major, stride FX) and four strips outside it,
     // top (j = FY+2), left (i = 1), bottom (j = 1), right (i = FX+2); the corners are never
-    // read and not kept.  With stride FX an 8 x 4 block of cells is one conflict-free row of
-    // banks; the slot stride is padded by 16 floats (faces whose two sides lie in adjacent
-    // slots, and warps that straddle two planes, then meet fewer bank conflicts).
+    // read and not kept.  The interior is row-major with the halves of rows 4..7 swapped
+    // (see qx in the kernel); the slot stride is padded by 16 floats (faces whose two sides
+    // lie in adjacent slots, and warps that straddle two planes, then meet fewer bank
+    // conflicts).
     static constexpr int QC = FX * FY + 2 * (FX + FY);
     static constexpr int QT = FX * FY, QL = QT + FX, QB = QL + FY, QR = QB + FX;
     static constexpr int QS = 4 * NV * QC + 16;
@@ -126,6 +127,11 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
     auto Qp = [&](int slot) { return reinterpret_cast<R (*)[QC]>(sm.Q[slot]); };
+    // Q index of interior cell (ix, iy): row-major, the two 4-cell halves of a row swapped
+    // in rows 4..7, so that a 4 x 8 block (the predictor's stores) and 8 x 4 blocks (the
+    // faces' loads) each fall on 32 distinct banks
+    static_assert(FX == 8, "the interior swizzle assumes rows of two 4-cell halves");
+    auto qx = [](int ix, int iy) { return (ix ^ (((iy >> 2) & 1) << 2)) + FX * iy; };
     const TreeView &tv = a.tv;
     const int tid = threadIdx.x, nt = blockDim.x;
     Prm<R> pr;
@@ -228,9 +234,15 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             for (int r2 = tid; r2 < 2 * QC; r2 += nt) {
                 const int dp = r2 >= QC, r = r2 - dp * QC, p = p0 + dp;
                 const int s0 = p & 3, sm1 = (p - 1) & 3, sp1 = (p + 1) & 3, qs = q3(p);
-                // item r is the cell kept at Q index r
-                int i, j;
-                if (r < QT) { i = 2 + r % FX; j = 2 + r / FX; }
+                // item r: interior cells in blocks 4 wide and FY tall (an 8 x 4 block with
+                // the W row stride of 12 would meet 2-way bank conflicts on every load),
+                // then the strips, each cell at Q index qi
+                int i, j, qi = r;
+                static_assert(FX % 4 == 0, "interior blocks are 4 cells wide");
+                if (r < QT) {
+                    const int ix = 4 * (r / (4 * FY)) + r % 4, iy = (r / 4) % FY;
+                    i = 2 + ix; j = 2 + iy; qi = qx(ix, iy);
+                }
                 else if (r < QL) { i = 2 + (r - QT); j = FY + 2; }
                 else if (r < QB) { i = 1; j = 2 + (r - QL); }
                 else if (r < QR) { i = 2 + (r - QB); j = 1; }
@@ -254,11 +266,11 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 Wt[4] = pp - hl * (u * Dl[0][4] + vv * Dl[1][4] + w * Dl[2][4] + pr.gamma * pp * (Dl[0][1] + Dl[1][2] + Dl[2][3]));
                 R (*Qs)[QC] = Qp(qs);
 #pragma unroll
-                for (int v = 0; v < NV; ++v) Qs[v][r] = Wt[v];
+                for (int v = 0; v < NV; ++v) Qs[v][qi] = Wt[v];
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) Qs[NV + NV * d + v][r] = Dl[d][v];
+                    for (int v = 0; v < NV; ++v) Qs[NV + NV * d + v][qi] = Dl[d][v];
             }
         };
         // z faces below planes j (face j-1 | j), for the listed planes
@@ -266,9 +278,9 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             const int qa = q3(j0 - 1), qb = q3(j0), qc = q3(j0 + 1);
             for (int r = tid; r < count * FX * FY; r += nt) {
                 const int dj = r / (FX * FY);          // FX * FY is a power of two
-                const int rr = r % (FX * FY);
+                const int rr = r % (FX * FY), qz = qx(rr % FX, rr / FX);
                 R WL[NV], WR[NV], Fn[NV];
-                col_face<R, 2, QC>(Qp(dj ? qb : qa), Qp(dj ? qc : qb), rr, rr, pr, WL, WR);
+                col_face<R, 2, QC>(Qp(dj ? qb : qa), Qp(dj ? qc : qb), qz, qz, pr, WL, WR);
                 col_solve<R, RS>(WL, WR, pr, a.status, Fn);
                 col_store<2>(sm.Fz[dj ? qc : qb], rr, Fn);
             }
@@ -294,8 +306,14 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                     // cell rr, else the face on the left of interior column 0 in row rr - FX*FY
                     kind = 0; dz = r / NXF; rr = r % NXF;
                     int pl, pq;
-                    if (rr < QT) { pl = rr; pq = rr % FX == FX - 1 ? QR + rr / FX : rr + 1; }
-                    else { pl = QL + (rr - QT); pq = FX * (rr - QT); }
+                    if (rr < QT) {
+                        const int ix = rr % FX, iy = rr / FX;
+                        pl = qx(ix, iy);
+                        pq = ix == FX - 1 ? QR + iy : qx(ix + 1, iy);
+                    } else {
+                        pl = QL + (rr - QT);
+                        pq = qx(0, rr - QT);
+                    }
                     const int qs = dz ? qk1 : qk0;
                     col_face<R, 0, QC>(Qp(qs), Qp(qs), pl, pq, pr, WL, WR);
                 } else if (r < 2 * (NXF + NYF)) {
@@ -303,14 +321,15 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                     const int r2 = r - 2 * NXF;
                     kind = 1; dz = r2 / NYF; rr = r2 % NYF;
                     const int col = rr % FX, fa = rr / FX;
-                    const int pl = fa == 0 ? QB + col : rr - FX, pq = fa == FY ? QT + col : rr;
+                    const int pl = fa == 0 ? QB + col : qx(col, fa - 1), pq = fa == FY ? QT + col : qx(col, fa);
                     const int qs = dz ? qk1 : qk0;
                     col_face<R, 1, QC>(Qp(qs), Qp(qs), pl, pq, pr, WL, WR);
                 } else {
                     // the face below plane k+1+dz: between planes k+dz and k+1+dz
                     const int r2 = r - 2 * (NXF + NYF);
                     kind = 2; dz = r2 / (FX * FY); rr = r2 % (FX * FY);
-                    col_face<R, 2, QC>(Qp(dz ? qk1 : qk0), Qp(dz ? qk2 : qk1), rr, rr, pr, WL, WR);
+                    const int qz = qx(rr % FX, rr / FX);
+                    col_face<R, 2, QC>(Qp(dz ? qk1 : qk0), Qp(dz ? qk2 : qk1), qz, qz, pr, WL, WR);
                 }
                 col_solve<R, RS>(WL, WR, pr, a.status, Fn);
                 if (kind == 0) col_store<0>(sm.Fx[dz], rr, Fn);

@@ -142,6 +142,9 @@ def time_path(H, tree, prm, w0, steps, warmup, stream, label, kernel_events=True
     """Run warmup + timed steps; returns (ms_per_step, godunov_ms_per_launch, sim)."""
     import torch
     sim = H.Simulation(tree, prm, w0=w0)
+    # the initial state and dt are made on the current stream; the steps below run on
+    # `stream`, which does not wait for it by itself
+    stream.wait_stream(torch.cuda.current_stream())
     nlev = tree.levelmax
 
     def one_step(ev=None):

@@ -29,13 +29,23 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
+def _code_only(text):
+    """Source text without comments and blank space (a change of comments leaves the
+    compiled kernel, and so its profiler counters, unchanged)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_hash():
-    """Hash of the sources the z-column update kernel (the benchmark's dominant kernel) is
-    compiled from: ties its recorded profiler counters to a kernel version."""
+    """Hash of the code the z-column update kernel (the benchmark's dominant kernel) is
+    compiled from, comments excluded: ties its recorded profiler counters to a kernel
+    version."""
     import hashlib
     h = hashlib.sha256()
     for f in ("common.cuh", "godunov_col.cuh", "hydro_math.cuh"):
-        h.update(open(os.path.join(CSRC, f), "rb").read())
+        h.update(_code_only(open(os.path.join(CSRC, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -20,12 +20,11 @@ template <typename R, int FX, int FY, bool FINER> struct ColSmem {
     static constexpr int SX = FX + 4, SY = FY + 4;   // stencil footprint (cells)
     R W[4][NV][SY * SX];                             // ring, slot = plane & 3 (live: k .. k+3)
     // Q ring, slot = (plane + 6) % 3 (live: k .. k+2).  A plane keeps the predicted cells the
-    // faces read: the FX x FY interior (row-major, stride FX) and four strips outside it,
-    // top (j = FY+2), left (i = 1), bottom (j = 1), right (i = FX+2); the corners are never
-    // read and not kept.  The interior is row-major with the halves of rows 4..7 swapped
-    // (see qx in the kernel); the slot stride is padded by 16 floats (faces whose two sides
-    // lie in adjacent slots, and warps that straddle two planes, then meet fewer bank
-    // conflicts).
+    // faces read: the FX x FY interior and four strips outside it, top (j = FY+2), left
+    // (i = 1), bottom (j = 1), right (i = FX+2); the corners are never read and not kept.
+    // The interior is row-major (stride FX) with the two halves of rows 4..7 swapped (qx in
+    // the kernel); the slot stride is padded by 16 floats (faces whose two sides lie in
+    // adjacent slots, and warps that straddle two planes, then meet fewer bank conflicts).
     static constexpr int QC = FX * FY + 2 * (FX + FY);
     static constexpr int QT = FX * FY, QL = QT + FX, QB = QL + FY, QR = QB + FX;
     static constexpr int QS = 4 * NV * QC + 16;
@@ -41,7 +40,7 @@ template <typename R, int FX, int FY, bool FINER> struct ColSmem {
     int32_t cell0[2][NOS];                           // cell id of each oct's child 0 (-1: refined)
     int32_t oct[4][(SX / 2) * (SY / 2)];             // oct id per footprint oct column, slot = oct layer & 3
     // refined flag of each stencil cell, slot = plane & 7 (live: k-1 .. k+5, longer than the
-    // W ring); only when the level has finer levels (keeps 4 CTAs per SM otherwise)
+    // W ring); only when the level has finer levels
     uint8_t ref[FINER ? 8 : 1][FINER ? SY * SX : 1];
 };
 

@@ -393,3 +393,50 @@ class Simulation:
         w = torch.empty_like(self.u)
         hydro_prim_of_state(self.tree, self.prm, self.u, w)
         return w
+
+
+# ---------------------------------------------------------------------------------------
+# Checkpoint / resume: a snapshot of a run through the host, in one .npz file.
+
+CHECKPOINT_VERSION = 1
+
+
+def save_checkpoint(path, sim):
+    """Write the octree's oct list (level, ix, iy, iz per oct; the box sizes in batch
+    mode), its levelmin and boundary codes, the FP64 state, the time step(s) of the next
+    step, the step count and the time.  The oct list rebuilds the same tree, so a run
+    resumed from the file continues bit for bit."""
+    tree = sim.tree
+    torch.cuda.synchronize(tree.device)
+    rec = {"version": np.int32(CHECKPOINT_VERSION), "bc": np.array(tree.t.bc[:], dtype=np.int32),
+           "levelmin": np.int32(tree.levelmin), "u": sim.u.cpu().numpy(), "dt": sim.dt.cpu().numpy(),
+           "nsteps": np.int64(sim.nsteps), "time": np.float64(sim.time)}
+    if tree.n_inst > 0:
+        rec["sizes"] = np.asarray(tree.sizes, dtype=np.int32)
+    else:
+        tab = tree.tables()
+        rec["lxyz"] = torch.stack([tab["lvl"], tab["ix"], tab["iy"], tab["iz"]], dim=1).cpu().numpy()
+    with open(path, "wb") as f:
+        np.savez(f, **rec)
+
+
+def load_checkpoint(path, prm, device="cuda:0"):
+    """Rebuild the octree and the run of a checkpoint written by save_checkpoint;
+    returns the Simulation (prm gives the scheme's parameters, which the file does not
+    hold)."""
+    with np.load(path) as z:
+        if int(z["version"]) != CHECKPOINT_VERSION:
+            raise ValueError("checkpoint version %d, expected %d" % (int(z["version"]), CHECKPOINT_VERSION))
+        bc = tuple(int(b) for b in z["bc"])
+        if "sizes" in z:
+            tree = Octree.boxes(z["sizes"], bc=bc, device=device)
+        else:
+            tree = Octree(z["lxyz"], int(z["levelmin"]), bc, device=device)
+        u = torch.as_tensor(z["u"]).to(tree.device)
+        if tuple(u.shape) != (5, tree.ncell):
+            raise ValueError("checkpoint state has shape %s, the rebuilt tree %d cells" % (tuple(u.shape), tree.ncell))
+        sim = Simulation(tree, prm, u0=u)
+        sim.dt.copy_(torch.as_tensor(z["dt"]))
+        sim.nsteps = int(z["nsteps"])
+        sim.time = float(z["time"])
+    return sim

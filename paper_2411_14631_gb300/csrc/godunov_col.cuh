@@ -259,9 +259,10 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 const R rr = Wc[0], u = Wc[1], vv = Wc[2], w = Wc[3], pp = Wc[4];
                 R Wt[NV];
                 Wt[0] = rr - hl * (u * Dl[0][0] + rr * Dl[0][1] + vv * Dl[1][0] + rr * Dl[1][2] + w * Dl[2][0] + rr * Dl[2][3]);
-                Wt[1] = u - hl * (u * Dl[0][1] + vv * Dl[1][1] + w * Dl[2][1] + Dl[0][4] / rr);
-                Wt[2] = vv - hl * (u * Dl[0][2] + vv * Dl[1][2] + w * Dl[2][2] + Dl[1][4] / rr);
-                Wt[3] = w - hl * (u * Dl[0][3] + vv * Dl[1][3] + w * Dl[2][3] + Dl[2][4] / rr);
+                const R ir = R(1) / rr;
+                Wt[1] = u - hl * (u * Dl[0][1] + vv * Dl[1][1] + w * Dl[2][1] + Dl[0][4] * ir);
+                Wt[2] = vv - hl * (u * Dl[0][2] + vv * Dl[1][2] + w * Dl[2][2] + Dl[1][4] * ir);
+                Wt[3] = w - hl * (u * Dl[0][3] + vv * Dl[1][3] + w * Dl[2][3] + Dl[2][4] * ir);
                 Wt[4] = pp - hl * (u * Dl[0][4] + vv * Dl[1][4] + w * Dl[2][4] + pr.gamma * pp * (Dl[0][1] + Dl[1][2] + Dl[2][3]));
                 R (*Qs)[QC] = Qp(qs);
 #pragma unroll

@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(256) k_ghost(TreeView tv, const double *__rest
 template <typename R>
 __device__ __forceinline__ void cons_to_prim_w(const R U[NV], const Prm<R> &p, R W[NV])
 {
-    const R rho = rmax(U[0], p.rho_floor);
-    const R u = U[1] / rho, v = U[2] / rho, w = U[3] / rho;
+    const R rho = rmax(U[0], p.rho_floor), irho = R(1) / rho;
+    const R u = U[1] * irho, v = U[2] * irho, w = U[3] * irho;
     const R ek = R(0.5) * rho * (u * u + v * v + w * w);
     const R pr = (p.gamma - R(1)) * (U[4] - ek);
     W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
@@ -461,9 +461,10 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
             const R r = Wc[0], u = Wc[1], vv = Wc[2], w = Wc[3], pp = Wc[4];
             R Wt[NV];
             Wt[0] = r - hl * (u * Dl[0][0] + r * Dl[0][1] + vv * Dl[1][0] + r * Dl[1][2] + w * Dl[2][0] + r * Dl[2][3]);
-            Wt[1] = u - hl * (u * Dl[0][1] + vv * Dl[1][1] + w * Dl[2][1] + Dl[0][4] / r);
-            Wt[2] = vv - hl * (u * Dl[0][2] + vv * Dl[1][2] + w * Dl[2][2] + Dl[1][4] / r);
-            Wt[3] = w - hl * (u * Dl[0][3] + vv * Dl[1][3] + w * Dl[2][3] + Dl[2][4] / r);
+            const R ir = R(1) / r;
+            Wt[1] = u - hl * (u * Dl[0][1] + vv * Dl[1][1] + w * Dl[2][1] + Dl[0][4] * ir);
+            Wt[2] = vv - hl * (u * Dl[0][2] + vv * Dl[1][2] + w * Dl[2][2] + Dl[1][4] * ir);
+            Wt[3] = w - hl * (u * Dl[0][3] + vv * Dl[1][3] + w * Dl[2][3] + Dl[2][4] * ir);
             Wt[4] = pp - hl * (u * Dl[0][4] + vv * Dl[1][4] + w * Dl[2][4] + pr.gamma * pp * (Dl[0][1] + Dl[1][2] + Dl[2][3]));
 #pragma unroll
             for (int v = 0; v < NV; ++v) sm.Q[v][p] = Wt[v];

@@ -72,8 +72,8 @@ template <typename R> __device__ __forceinline__ R slope(const Prm<R> &p, R a, R
 template <typename R>
 __device__ __forceinline__ void cons_to_prim(const double U[NV], const Prm<R> &p, R W[NV])
 {
-    const R rho = rmax(to_work<R>(U[0]), p.rho_floor);
-    const R u = to_work<R>(U[1]) / rho, v = to_work<R>(U[2]) / rho, w = to_work<R>(U[3]) / rho;
+    const R rho = rmax(to_work<R>(U[0]), p.rho_floor), irho = R(1) / rho;
+    const R u = to_work<R>(U[1]) * irho, v = to_work<R>(U[2]) * irho, w = to_work<R>(U[3]) * irho;
     const R ek = R(0.5) * rho * (u * u + v * v + w * w);
     const R pr = (p.gamma - R(1)) * (to_work<R>(U[4]) - ek);
     W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
@@ -104,7 +104,8 @@ __device__ __forceinline__ void hllc(const R WL[NV], const R WR[NV], R g, R F[NV
     const R cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
     const R SL = fmin(uL - cL, uR - cR);
     const R SR = fmax(uL + cL, uR + cR);
-    const R Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR));
+    const R mL = rL * (SL - uL), mR = rR * (SR - uR);   // mass fluxes through the outer waves
+    const R Ss = (pR - pL + uL * mL - uR * mR) / (mL - mR);
     const bool left = (SL >= R(0)) || (Ss >= R(0));
     const bool star = !(SL >= R(0)) && (Ss >= R(0) || SR > R(0));
     R WK[NV];
@@ -114,10 +115,14 @@ __device__ __forceinline__ void hllc(const R WL[NV], const R WR[NV], R g, R F[NV
     R FK[NV], UK[NV];
     flux_normal(WK, g, FK, UK);
     if (star) {
+        // U*_K = f [1, S*, v_K, w_K, E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))],
+        // f = rho_K (S_K - u_K) / (S_K - S*); with d = 1/(S_K - S*) the energy component is
+        // d ((S_K - u_K) E_K + (S* - u_K) p_K) + f (S* - u_K) S*, one division in all
         const R rK = WK[0], uK = WK[1], pK = WK[4];
-        const R f = rK * (SK - uK) / (SK - Ss);
+        const R d = R(1) / (SK - Ss);
+        const R f = rK * (SK - uK) * d;
         const R Us[NV] = {f, f * Ss, f * WK[2], f * WK[3],
-                          f * (UK[4] / rK + (Ss - uK) * (Ss + pK / (rK * (SK - uK))))};
+                          d * ((SK - uK) * UK[4] + (Ss - uK) * pK) + f * (Ss - uK) * Ss};
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = FK[v] + SK * (Us[v] - UK[v]);
     } else {

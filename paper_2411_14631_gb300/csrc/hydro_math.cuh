@@ -15,12 +15,13 @@ namespace amr {
 // normal floats, zero for zero and FP32 denormals.
 __device__ __forceinline__ float d2f_bits(double x)
 {
-    const unsigned hi = unsigned(__double2hiint(x)), lo = unsigned(__double2loint(x));
-    const unsigned ahi = hi & 0x7FFFFFFFu;
-    unsigned m = __funnelshift_l(lo, ahi, 3) - (896u << 23);   // rebias 1023 -> 127, keep 23 mantissa bits
-    m += (lo >> 28) & 1u;
-    m = ahi < (897u << 20) ? 0u : m;
-    return __uint_as_float(m | (hi & 0x80000000u));
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long ab = b & 0x7FFFFFFFFFFFFFFFull;
+    // one 64-bit add rebiases the exponent (1023 -> 127) and rounds on the highest dropped
+    // bit; bits 29..60 are then the FP32 exponent and mantissa
+    unsigned m = unsigned((ab + ((1ull << 28) - (896ull << 52))) >> 29);
+    m = unsigned(ab >> 32) < (897u << 20) ? 0u : m;
+    return __uint_as_float(m | (unsigned(b >> 32) & 0x80000000u));
 }
 
 __device__ __forceinline__ double f2d_bits(float f)

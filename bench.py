@@ -265,7 +265,9 @@ def time_e2e(H, tree, prm, w0, steps, stream):
     return ms, nbytes, copy_ms
 
 
-def cpu_baseline(lx, rho, v, sample_steps=1):
+def cpu_baseline(lx, rho, v, min_seconds=10.0, max_steps=8):
+    """The FP64 oracle on the host cores: whole steps of the same box, as many as take at
+    least min_seconds (at most max_steps, at least one)."""
     import numpy as np
     import oracle as O
     from paper_2411_14631_gb300 import workloads as W
@@ -277,8 +279,12 @@ def cpu_baseline(lx, rho, v, sample_steps=1):
     u = t.init_from_prim(w, prm)
     leaf = int((t.son < 0).sum())
     t0 = time.perf_counter()
-    for _ in range(sample_steps):
+    sample_steps = 0
+    while sample_steps < max_steps:
         u, dt, st = t.step(u, prm)
+        sample_steps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": leaf * sample_steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",

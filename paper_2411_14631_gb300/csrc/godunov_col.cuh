@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
         };
         auto q3 = [](int p) { return (p + 6) % 3; };   // planes start at z0 - 2 >= -2
-        // MinMod slopes + MUSCL-Hancock predictor of planes p0 and p0+1 (cells 1..SX-2 x
-        // 1..SY-2 of each), one loop so that every warp of the CTA takes a share
+        // MinMod slopes + MUSCL-Hancock predictor of planes p0 and p0+1 (of each, the QC
+        // cells the faces read), one loop so that every warp of the CTA takes a share
         auto predict2 = [&](int p0, bool fill, int fillL) {
             // threads past the predictions fill the oct table of layer fillL
             if (fill)

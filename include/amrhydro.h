@@ -22,7 +22,8 @@
  *     The library never allocates device memory and never frees caller memory.
  *   - Calls that take a stream are asynchronous on it, make no host synchronisation
  *     and read the time step through a device pointer, so a sequence of them can be
- *     captured in a CUDA graph.  amr_build_octree and amr_get_status synchronise.
+ *     captured in a CUDA graph (hydro_step_static_scratch is not covered by this
+ *     statement).  amr_build_octree and amr_get_status synchronise.
  *   - Argument errors are returned at once.  Errors found on the device (a
  *     non-physical state, a failed exact solve) are written to params->d_status
  *     (first error wins) and read with amr_get_status.  Nothing aborts or traps.
@@ -47,7 +48,10 @@ typedef enum {
     AMR_ECAPACITY = -3,     /* a caller buffer is smaller than the query said */
     AMR_ECUDA = -4,         /* a CUDA runtime call failed */
     AMR_ETIMEOUT = -5,      /* a bounded device-side wait gave up */
-    AMR_ENONPHYSICAL = -6,  /* vacuum in an exact Riemann problem (HLLC flux used instead) */
+    AMR_ENONPHYSICAL = -6,  /* a non-physical state: vacuum in an exact Riemann problem (HLLC flux
+                               used instead), or a cell whose updated state is not finite in the
+                               working precision (NaN, +-Inf, or beyond FP32's range in the FP32
+                               path); the state is written as computed */
     AMR_ENOCONV = -7,       /* an iteration did not converge: the exact Riemann Newton iteration
                                (HLLC used instead), or a Poisson solve within its iteration cap */
     AMR_EBREAKDOWN = -8     /* a Poisson solve met a step length that is not positive and finite */
@@ -197,14 +201,25 @@ amr_status hydro_godunov_level(const amr_tree *tree, int level, const hydro_para
 
 size_t hydro_flux_reg_bytes(const amr_tree *tree);
 
-/* Refluxing and restriction for coarse level `level`, run from the finest level up
-   after every hydro_godunov_level of the step: each leaf cell of the level next to a
-   refined cell receives -/+ dt/dx * 1/4 * (sum of the four fine fluxes) from the flux
-   register; then each refined cell becomes the mean of its children.  d_dt_next as in
-   hydro_godunov_level, for the corrected cells. */
+/* Refluxing and restriction for coarse level `level` (1 <= level < levelmax): the part
+   of the level step of Table 1 (godunov_fine and its coarse-fine bookkeeping) that keeps
+   the octree scheme conservative; the method is RAMSES' AMR scheme (Teyssier 2002, the
+   code Sec. 1 builds on).  Run from the finest level up after every hydro_godunov_level
+   of the step: each leaf cell of the level next to a refined cell receives
+   -/+ dt/dx * 1/4 * (sum of the four fine fluxes) from the flux register d_flux_reg
+   (device, hydro_flux_reg_bytes, written by hydro_godunov_level in the same step; may be
+   NULL when level < levelmin); then each refined cell of the level becomes the mean of
+   its eight children, in d_u_new (device FP64 SoA, updated in place).  d_dt: the step's
+   device scalar time step; d_dt_next as in hydro_godunov_level, for the corrected cells.
+   AMR_EINVAL for a level outside 1 .. levelmax-1 or a missing buffer; asynchronous.
+   reflux_level is the same entry point under its shorter name; both names are
+   exported. */
 amr_status hydro_reflux_level(const amr_tree *tree, int level, const hydro_params *params,
                               const double *d_flux_reg, double *d_u_new, const double *d_dt,
                               double *d_dt_next, amr_stream stream);
+amr_status reflux_level(const amr_tree *tree, int level, const hydro_params *params,
+                        const double *d_flux_reg, double *d_u_new, const double *d_dt,
+                        double *d_dt_next, amr_stream stream);
 
 /* One whole step: resets *d_dt_next (if not NULL) to a large value, then godunov on
    every level (one launch), then reflux + restriction from the finest level up.
@@ -215,19 +230,22 @@ amr_status hydro_step(const amr_tree *tree, const hydro_params *params, const do
 
 /* hydro_step without any caller-provided scratch.  The paper has no counterpart: this
    is an interface convenience.  Some callers cannot allocate device memory when they
-   want to step: code that records the step inside CUDA stream capture (cudaMalloc is
-   not a capturable operation), real-time loops that forbid allocation after start-up,
-   and hosts whose device memory is owned by another framework's memory pool.  For them,
-   the flux register lives in a fixed array inside this library, sized for at most
-   AMR_STATIC_REG_MAX_OCTS octs above levelmin (31.5 MB, held by every GPU that loads
-   the library until the process exits).  Trees with more such octs, or whose register
-   with its ghost-children part (hydro_flux_reg_bytes) exceeds the array, get
-   AMR_ECAPACITY and nothing runs.  Inputs and outputs are the caller's, as for hydro_step.  The first
-   call on each device looks up the array's device address (no allocation); make that
-   first call before any stream capture.  Every call shares the one array: calls whose
-   work overlaps on the GPU (other streams, other host threads) race and give wrong
-   results.  No register row needs a starting value: every row read in a call is written
-   earlier in the same call. */
+   want to step: real-time loops that forbid allocation after start-up, and hosts whose
+   device memory is owned by another framework's memory pool (a second allocator would
+   fragment or overcommit it).  For them, the flux register lives in a fixed array inside
+   this library, sized for at most AMR_STATIC_REG_MAX_OCTS octs above levelmin (31.5 MB,
+   held by every GPU that loads the library until the process exits).  Trees with more
+   such octs, or whose register with its ghost-children part (hydro_flux_reg_bytes)
+   exceeds the array, get AMR_ECAPACITY and nothing runs.  Inputs and outputs are the
+   caller's, as for hydro_step; no call allocates or frees device memory.  The first
+   call on each device looks up the array's device address (no allocation) and caches
+   it; make that first call before any stream capture.  The set-up is safe when several
+   host threads make their first call at once.  cudaDeviceReset unloads the library's
+   device code, and the cached address then names memory that no longer exists: after a
+   reset this entry point must not be called again in the same process.  Every call
+   shares the one array: calls whose work overlaps on the GPU (other streams, other host
+   threads) race and give wrong results.  No register row needs a starting value: every
+   row read in a call is written earlier in the same call, so nothing is cleared. */
 #define AMR_STATIC_REG_MAX_OCTS 131072
 amr_status hydro_step_static_scratch(const amr_tree *tree, const hydro_params *params, const double *d_u_old,
                                      double *d_u_new, const double *d_dt, double *d_dt_next, amr_stream stream);
@@ -360,6 +378,38 @@ amr_status amr_build_octree_device(const amr_geom *geom, const int32_t *d_oct_lx
    AMR_EUNBALANCED to d_status (may be NULL). */
 amr_status amr_remap_state(const amr_tree *t_old, const double *d_u_old, const amr_tree *t_new, double *d_u_new,
                            int32_t *d_status, amr_stream stream);
+
+/* Global conservation diagnostics: the totals of the conserved variables over the leaf
+   cells, computed on the device in FP64.  The level step of Table 1 (godunov_fine with
+   its refluxing at coarse-fine faces; RAMSES' scheme, Teyssier 2002, on which Sec. 1
+   builds) conserves them up to rounding in a periodic box; the paper prints no formula,
+   the one computed is the plain definition.  d_totals (device double[nbox][2][5], nbox =
+   n_inst in batch mode, else 1): [b][0][v] = sum over the leaf cells of box b of
+   U_v dV and [b][1][v] = sum of |U_v| dV (v = rho, rho u, rho v, rho w, E; dV = dx_l^3,
+   or (1/N)^3 for a box of N^3 cells), the second a scale for the drift of the first.
+   The octs are cut into fixed chunks of 256 (per box), each summed in a fixed order (an
+   oct's cells in cell order, then a fixed tree over the chunk), and each box's chunk
+   sums are added in a fixed order: the result is the same bit for bit for every launch
+   shape.  blocks: CTAs of the chunk pass (0 = 4 per SM); it changes the speed, not the
+   result.  d_u: device FP64 SoA state (16-byte aligned); d_work: hydro_conservation_
+   work_bytes(tree) bytes of device scratch, 256-byte aligned.  AMR_EINVAL for a missing
+   or misaligned buffer or blocks < 0, AMR_ECAPACITY for a short d_work.  No atomics, no
+   host synchronisation; asynchronous on the stream. */
+size_t hydro_conservation_work_bytes(const amr_tree *tree);
+amr_status hydro_conservation(const amr_tree *tree, const double *d_u, double *d_totals, void *d_work,
+                              size_t work_bytes, int32_t blocks, amr_stream stream);
+
+/* The FP32 path's conversions of state values, exposed so that they can be checked
+   against IEEE conversions; the paper has no counterpart (its code is FP64 throughout).
+   hydro_state_to_fp32: d_y[i] = the FP32 value the FP32 path reads for the FP64 state
+   value d_x[i]: round to nearest, ties away from zero (IEEE rounds ties to even); |x|
+   below 2^-126 gives a signed zero; |x| >= 2^128, +-Inf and NaN give a non-finite float
+   of the same sign (+-Inf or a NaN).  hydro_state_from_fp32: d_x[i] = the FP64 value of
+   the FP32 value d_y[i] (exact; +-Inf and NaN kept; FP32 denormals give a signed zero).
+   Device arrays of n >= 0 elements; AMR_EINVAL for n < 0 or a NULL array with n > 0;
+   asynchronous on the stream. */
+amr_status hydro_state_to_fp32(const double *d_x, float *d_y, int64_t n, amr_stream stream);
+amr_status hydro_state_from_fp32(const float *d_y, double *d_x, int64_t n, amr_stream stream);
 
 /* Copy params->d_status and params->d_counters to the host (synchronises the device). */
 amr_status amr_get_status(const hydro_params *params, int32_t *h_status, unsigned long long *h_counters);

@@ -12,6 +12,7 @@ solvers in ``riemann.c``; the octree and Hilbert key in ``tree.c``; the surrogat
 network in ``mlp.c``; the CG and PPCG Poisson solvers of Sec. 2.3 in ``poisson.c``.
 """
 import ctypes as C
+import math
 import os
 import subprocess
 
@@ -246,11 +247,44 @@ class Tree:
         st = lib().or_remap(self._h, _p(u), new_tree._h, _p(un))
         return un, st
 
+    # ---- global conservation diagnostics ----------------------------------------------
+    def conservation_totals(self, u):
+        """[2][5]: the sum over the leaf cells of U_v dV (dV = dx_l^3 = 2^-3l) and of
+        |U_v| dV, each exactly rounded (math.fsum): the plain definition of the leaf totals
+        that the level step (Table 1, godunov_fine with refluxing) conserves, with no
+        summation order of its own."""
+        u = _f64(u)
+        leaf = self.son < 0
+        dV = np.ldexp(1.0, -3 * np.repeat(self.lvl, 8).astype(np.int64))[leaf]
+        out = np.empty((2, 5))
+        for v in range(5):
+            x = u[v, leaf] * dV                  # exact: dV is a power of two
+            out[0, v] = math.fsum(x.tolist())
+            out[1, v] = math.fsum(np.abs(x).tolist())
+        return out
+
     def stencil(self, u, oct_id):
         u = _f64(u)
         s = np.empty(5 * 216)
         st = lib().or_oct_stencil(self._h, _p(u), oct_id, _p(s))
         return s.reshape(5, 6, 6, 6), st
+
+
+def box_conservation_totals(sizes, u):
+    """[nbox][2][5] for a batch of uniform boxes of sizes[b]^3 cells stored one after the
+    other: sum over box b's cells of U_v / N^3 and of |U_v| / N^3, as the exactly rounded
+    sum (math.fsum) divided by the integer N^3 (one more rounding)."""
+    u = _f64(u)
+    out = np.empty((len(sizes), 2, 5))
+    c0 = 0
+    for b, N in enumerate(sizes):
+        n = int(N) ** 3
+        for v in range(5):
+            x = u[v, c0:c0 + n]
+            out[b, 0, v] = math.fsum(x.tolist()) / n
+            out[b, 1, v] = math.fsum(np.abs(x).tolist()) / n
+        c0 += n
+    return out
 
 
 def hilbert_key(bits, x, y, z):

@@ -19,13 +19,14 @@ PRECOND_NONE, PRECOND_IP = 0, 1
 OP_A, OP_MINV = 0, 1
 
 EXPORTS = ["amr_build_octree_query", "amr_build_octree", "hydro_init_from_prim", "hydro_prim_of_state",
-           "hydro_courant", "hydro_godunov_level", "hydro_flux_reg_bytes", "hydro_reflux_level", "hydro_step",
+           "hydro_courant", "hydro_godunov_level", "hydro_flux_reg_bytes", "hydro_reflux_level", "reflux_level", "hydro_step",
            "amr_get_status", "amr_status_string", "hydro_step_static_scratch", "hydro_harvest_faces",
            "mlp_nparams", "mlp_packed_bytes", "mlp_scratch_bytes", "mlp_pack", "mlp_make_dataset", "mlp_forward",
            "mlp_grad", "mlp_train_step",
            "ppcg_workspace_bytes", "poisson_apply", "ppcg_start", "ppcg_iterate", "ppcg_poll", "ppcg_solve",
            "amr_refine_work_bytes", "amr_refine", "amr_build_octree_device_query", "amr_build_octree_device",
-           "amr_remap_state", "hydro_courant_levels", "hydro_step_subcycled"]
+           "amr_remap_state", "hydro_courant_levels", "hydro_step_subcycled", "hydro_state_to_fp32",
+           "hydro_state_from_fp32", "hydro_conservation_work_bytes", "hydro_conservation"]
 MLP_NPARAMS = 8962
 STATIC_REG_MAX_OCTS = 131072
 
@@ -93,6 +94,7 @@ def lib():
     L.hydro_flux_reg_bytes.argtypes = [PT]
     L.hydro_flux_reg_bytes.restype = S
     L.hydro_reflux_level.argtypes = [PT, C.c_int, PP, P, P, P, P, P]
+    L.reflux_level.argtypes = [PT, C.c_int, PP, P, P, P, P, P]
     L.hydro_step.argtypes = [PT, PP, P, P, P, P, P, P]
     L.hydro_step_static_scratch.argtypes = [PT, PP, P, P, P, P, P]
     L.hydro_harvest_faces.argtypes = [PT, PP, P, P, P, C.c_int64, C.c_int64, P, P]
@@ -123,12 +125,17 @@ def lib():
     L.ppcg_iterate.argtypes = [PG, P, P, S, P, I, P]
     L.ppcg_poll.argtypes = [P, C.POINTER(PpcgInfo), P]
     L.ppcg_solve.argtypes = [PG, P, P, P, S, P, C.POINTER(PpcgInfo), P]
+    L.hydro_conservation_work_bytes.argtypes = [PT]
+    L.hydro_conservation_work_bytes.restype = S
+    L.hydro_conservation.argtypes = [PT, P, P, P, S, C.c_int32, P]
+    L.hydro_state_to_fp32.argtypes = [P, P, C.c_int64, P]
+    L.hydro_state_from_fp32.argtypes = [P, P, C.c_int64, P]
     L.amr_get_status.argtypes = [PP, P, P]
     L.amr_status_string.argtypes = [C.c_int]
     L.amr_status_string.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("hydro_flux_reg_bytes", "amr_status_string", "mlp_packed_bytes", "mlp_scratch_bytes",
-                        "ppcg_workspace_bytes", "amr_refine_work_bytes"):
+                        "ppcg_workspace_bytes", "amr_refine_work_bytes", "hydro_conservation_work_bytes"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -385,6 +385,7 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                 un[v][cid] = Un[v];
                 sm.U[ub][uc][uo8 * NV + v] = Un[v];
             }
+            if (!state_finite<R>(Un)) set_error(a.status, AMR_ENONPHYSICAL);
             if (uc == 0) sm.cell0[ub][uo8] = cid;
             if (dtn && !nbref) my_dt = min(my_dt, (unsigned long long)__double_as_longlong(cfl_candidate<R>(Un, pr, cflR, dxR)));
         };

@@ -536,6 +536,7 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
                 else Un[v] = a.u_old[v * tv.ncell + cell] + to_state(lamR * dU[v]);
                 a.u_new[v * tv.ncell + cell] = Un[v];
             }
+            if (!state_finite<R>(Un)) set_error(a.status, AMR_ENONPHYSICAL);
             if (tv.fused[e]) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) sU[v][q] = Un[v];   // kept for the restriction pass

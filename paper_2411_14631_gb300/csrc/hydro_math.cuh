@@ -10,27 +10,55 @@ namespace amr {
 
 // FP64 <-> FP32 by integer bit manipulation.  On sm_103a the hardware conversions run on
 // the FP64 pipe (about 2 per clock per SM), as slow as FP64 arithmetic; these run on the
-// integer ALUs.  d2f: round to nearest on the dropped bits (ties away from zero); values
-// below the FP32 normal range become zero; |x| must be below 2^128.  f2d: exact for
-// normal floats, zero for zero and FP32 denormals.
+// integer ALUs.
+// d2f: round to nearest on the dropped bits, ties away from zero (the hardware rounds
+// ties to even; the two differ only when the 29 dropped bits are exactly 1 followed by
+// zeros); |x| below the FP32 normal range (2^-126) gives a signed zero; |x| >= 2^128,
+// +-Inf and NaN give a non-finite float of the same sign (+-Inf or a NaN: the magnitude's
+// high word is clamped to that of 2^128, so only the low word's bits decide which).
+// Finite x below 2^128 that round past FLT_MAX give +-Inf, as in the hardware.
+// f2d: exact for normal floats and for +-Inf; NaN stays NaN (payload kept); zero and
+// FP32 denormals give a signed zero.
 __device__ __forceinline__ float d2f_bits(double x)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long ab = b & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
+    const unsigned ahi = min(hi & 0x7FFFFFFFu, 0x47F00000u);
+    const unsigned long long ab = (static_cast<unsigned long long>(ahi) << 32) | lo;
     // one 64-bit add rebiases the exponent (1023 -> 127) and rounds on the highest dropped
     // bit; bits 29..60 are then the FP32 exponent and mantissa
     unsigned m = unsigned((ab + ((1ull << 28) - (896ull << 52))) >> 29);
-    m = unsigned(ab >> 32) < (897u << 20) ? 0u : m;
-    return __uint_as_float(m | (unsigned(b >> 32) & 0x80000000u));
+    m = ahi < (897u << 20) ? 0u : m;
+    return __uint_as_float(m | (hi & 0x80000000u));
 }
 
 __device__ __forceinline__ double f2d_bits(float f)
 {
     const unsigned b = __float_as_uint(f), ab = b & 0x7FFFFFFFu;
     const bool z = ab < 0x00800000u;
-    const unsigned hi = z ? 0u : (ab >> 3) + (896u << 20);
+    // exponent 255 (Inf, NaN) moves to 2047: one more rebias of 896
+    const unsigned bias = ab >= 0x7F800000u ? (1792u << 20) : (896u << 20);
+    const unsigned hi = z ? 0u : (ab >> 3) + bias;
     const unsigned lo = z ? 0u : ab << 29;
     return __hiloint2double(int(hi | (b & 0x80000000u)), int(lo));
+}
+
+// whether the five values of an FP64 state are finite in the working precision R: for
+// FP64 by the exponent fields of the high words (integer operations, off the FP64 pipe);
+// for FP32 by the sum of the converted values (non-finite when any of them is, or when
+// the state lies beyond FP32's range)
+template <typename R> __device__ __forceinline__ bool state_finite(const double U[5]);
+template <> __device__ __forceinline__ bool state_finite<double>(const double U[5])
+{
+    unsigned e = 0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) e = max(e, unsigned(__double2hiint(U[v])) & 0x7FF00000u);
+    return e < 0x7FF00000u;
+}
+template <> __device__ __forceinline__ bool state_finite<float>(const double U[5])
+{
+    const float s = (d2f_bits(U[0]) + d2f_bits(U[1])) + (d2f_bits(U[2]) + d2f_bits(U[3])) + d2f_bits(U[4]);
+    return fabsf(s) <= 3.402823466e38f;
 }
 
 // working-precision view of an FP64 state value, and back

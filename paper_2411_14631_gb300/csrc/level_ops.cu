@@ -1,7 +1,9 @@
 // Per-level operations around the Godunov update: the CFL time step (newdt_fine,
 // Table 1), refluxing + restriction, initial-state set-up, and the C entry points.
+#include <atomic>
 #include <cfloat>
 #include <cstring>
+#include <mutex>
 #include "hydro_math.cuh"
 
 namespace amr {
@@ -177,6 +179,18 @@ __global__ void k_cons_to_prim(int64_t ncell, const double *__restrict__ u, doub
     for (int v = 0; v < NV; ++v) w[v * ncell + i] = W[v];
 }
 
+__global__ void k_to_fp32(int64_t n, const double *__restrict__ x, float *__restrict__ y)
+{
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        y[i] = d2f_bits(x[i]);
+}
+
+__global__ void k_from_fp32(int64_t n, const float *__restrict__ y, double *__restrict__ x)
+{
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        x[i] = f2d_bits(y[i]);
+}
+
 static amr_status check(const amr_tree *t, const hydro_params *p)
 {
     if (!t || !p || t->noct <= 0) return AMR_EINVAL;
@@ -293,6 +307,12 @@ extern "C" amr_status hydro_reflux_level(const amr_tree *t, int level, const hyd
     return reflux_launch(t, level, p, d_flux_reg, d_u_new, d_dt, d_dt_next, reinterpret_cast<cudaStream_t>(stream));
 }
 
+extern "C" amr_status reflux_level(const amr_tree *t, int level, const hydro_params *p, const double *d_flux_reg,
+                                   double *d_u_new, const double *d_dt, double *d_dt_next, amr_stream stream)
+{
+    return hydro_reflux_level(t, level, p, d_flux_reg, d_u_new, d_dt, d_dt_next, stream);
+}
+
 // ---- sub-cycled step -----------------------------------------------------------------
 static amr_status sc_advance(const amr_tree *t, const hydro_params *p, int c, double *U, double *N, double *reg,
                              double *dtl, cudaStream_t st)
@@ -377,9 +397,29 @@ extern "C" amr_status hydro_step(const amr_tree *t, const hydro_params *p, const
 // For callers that cannot allocate device memory when they step.  The register is a
 // fixed file-scope device array; host code must not pass the symbol itself to a kernel
 // (in host code it names a host-side stand-in), so its device address is looked up once
-// per device and cached.
+// per device, with that device current, and cached.  The cache is an atomic per device;
+// the first look-up on a device runs under a mutex, so concurrent first calls from
+// several host threads are safe.
 static __device__ __align__(256) double g_static_reg[size_t(AMR_STATIC_REG_MAX_OCTS) * 6 * NV];
-static double *g_static_reg_addr[256];
+static std::atomic<double *> g_static_reg_addr[256];
+static std::mutex g_static_reg_mu;
+
+static amr_status static_reg_address(int dev, double **out)
+{
+    double *a = g_static_reg_addr[dev].load(std::memory_order_acquire);
+    if (!a) {
+        std::lock_guard<std::mutex> lock(g_static_reg_mu);
+        a = g_static_reg_addr[dev].load(std::memory_order_relaxed);
+        if (!a) {
+            void *addr = nullptr;
+            AMR_CUDA_TRY(cudaGetSymbolAddress(&addr, g_static_reg));
+            a = static_cast<double *>(addr);
+            g_static_reg_addr[dev].store(a, std::memory_order_release);
+        }
+    }
+    *out = a;
+    return AMR_OK;
+}
 
 extern "C" amr_status hydro_step_static_scratch(const amr_tree *t, const hydro_params *p, const double *d_u_old,
                                                 double *d_u_new, const double *d_dt, double *d_dt_next,
@@ -392,12 +432,10 @@ extern "C" amr_status hydro_step_static_scratch(const amr_tree *t, const hydro_p
     int dev = 0;
     AMR_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 256) return AMR_EINVAL;
-    if (!g_static_reg_addr[dev]) {
-        void *addr = nullptr;
-        AMR_CUDA_TRY(cudaGetSymbolAddress(&addr, g_static_reg));
-        g_static_reg_addr[dev] = static_cast<double *>(addr);
-    }
-    return hydro_step(t, p, d_u_old, d_u_new, g_static_reg_addr[dev], d_dt, d_dt_next, stream);
+    double *reg = nullptr;
+    const amr_status r = static_reg_address(dev, &reg);
+    if (r != AMR_OK) return r;
+    return hydro_step(t, p, d_u_old, d_u_new, reg, d_dt, d_dt_next, stream);
 }
 
 extern "C" amr_status hydro_harvest_faces(const amr_tree *t, const hydro_params *p, const double *d_u,
@@ -409,6 +447,26 @@ extern "C" amr_status hydro_harvest_faces(const amr_tree *t, const hydro_params 
     if (t->n_inst > 0) return AMR_EINVAL;   // octree runs only
     return harvest_dispatch(t, p, d_u, d_dt, d_states, capacity, stride, d_count,
                             reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" amr_status hydro_state_to_fp32(const double *d_x, float *d_y, int64_t n, amr_stream stream)
+{
+    if (n < 0 || (n > 0 && (!d_x || !d_y))) return AMR_EINVAL;
+    if (n == 0) return AMR_OK;
+    const int64_t nb = (n + 255) / 256;
+    k_to_fp32<<<unsigned(nb < 4096 ? nb : 4096), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(n, d_x, d_y);
+    AMR_CUDA_TRY(cudaGetLastError());
+    return AMR_OK;
+}
+
+extern "C" amr_status hydro_state_from_fp32(const float *d_y, double *d_x, int64_t n, amr_stream stream)
+{
+    if (n < 0 || (n > 0 && (!d_x || !d_y))) return AMR_EINVAL;
+    if (n == 0) return AMR_OK;
+    const int64_t nb = (n + 255) / 256;
+    k_from_fp32<<<unsigned(nb < 4096 ? nb : 4096), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(n, d_y, d_x);
+    AMR_CUDA_TRY(cudaGetLastError());
+    return AMR_OK;
 }
 
 extern "C" amr_status amr_get_status(const hydro_params *p, int32_t *h_status, unsigned long long *h_counters)
@@ -436,7 +494,7 @@ extern "C" const char *amr_status_string(int s)
     case AMR_ECAPACITY: return "caller buffer too small";
     case AMR_ECUDA: return "CUDA runtime error";
     case AMR_ETIMEOUT: return "device wait timed out";
-    case AMR_ENONPHYSICAL: return "vacuum in an exact Riemann problem";
+    case AMR_ENONPHYSICAL: return "non-physical state (exact-solver vacuum or a non-finite cell)";
     case AMR_ENOCONV: return "iteration did not converge";
     case AMR_EBREAKDOWN: return "Krylov iteration broke down";
     default: return "unknown status";

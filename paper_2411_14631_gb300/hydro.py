@@ -183,6 +183,13 @@ def hydro_reflux_level(tree, level, prm, reg, u_new, dt, dt_next=None, stream=No
                                    _ptr(dt_next), _stream(stream)))
 
 
+def reflux_level(tree, level, prm, reg, u_new, dt, dt_next=None, stream=None):
+    """hydro_reflux_level under its shorter exported name."""
+    check("reflux_level",
+          lib().reflux_level(C.byref(tree.t), level, C.byref(prm.c), _ptr(reg), _ptr(u_new), _ptr(dt),
+                             _ptr(dt_next), _stream(stream)))
+
+
 def hydro_step(tree, prm, u_old, u_new, reg, dt, dt_next=None, stream=None):
     check("hydro_step", lib().hydro_step(C.byref(tree.t), C.byref(prm.c), _ptr(u_old), _ptr(u_new), _ptr(reg),
                                          _ptr(dt), _ptr(dt_next), _stream(stream)))
@@ -194,6 +201,30 @@ def hydro_step_static_scratch(tree, prm, u_old, u_new, dt, dt_next=None, stream=
     check("hydro_step_static_scratch",
           lib().hydro_step_static_scratch(C.byref(tree.t), C.byref(prm.c), _ptr(u_old), _ptr(u_new), _ptr(dt),
                                           _ptr(dt_next), _stream(stream)))
+
+
+def hydro_conservation(tree, u, totals=None, work=None, blocks=0, stream=None):
+    """Leaf totals [nbox][2][5] on the device: sum U dV and sum |U| dV per box (see
+    include/amrhydro.h); returns the device tensor."""
+    nbox = max(1, tree.n_inst)
+    if totals is None:
+        totals = torch.empty((nbox, 2, 5), dtype=torch.float64, device=u.device)
+    if work is None:
+        work = torch.empty(int(lib().hydro_conservation_work_bytes(C.byref(tree.t))), dtype=torch.uint8,
+                           device=u.device)
+    check("hydro_conservation", lib().hydro_conservation(C.byref(tree.t), _ptr(u), _ptr(totals), _ptr(work),
+                                                         work.numel(), blocks, _stream(stream)))
+    return totals
+
+
+def hydro_state_to_fp32(x, y, stream=None):
+    """The FP32 path's FP64 -> FP32 conversion of state values (see include/amrhydro.h)."""
+    check("hydro_state_to_fp32", lib().hydro_state_to_fp32(_ptr(x), _ptr(y), x.numel(), _stream(stream)))
+
+
+def hydro_state_from_fp32(y, x, stream=None):
+    """The FP32 path's FP32 -> FP64 conversion (exact)."""
+    check("hydro_state_from_fp32", lib().hydro_state_from_fp32(_ptr(y), _ptr(x), y.numel(), _stream(stream)))
 
 
 def hydro_harvest_faces(tree, prm, u, dt, states, stride, count, stream=None):

@@ -34,6 +34,15 @@ def test_library_exports_every_declared_symbol(built):
     assert not missing, missing
 
 
+def test_scope_entry_points_are_exported(built):
+    """The four entry points of the hot path's boundary carry these exact names."""
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(\S+)", out))
+    for name in ("amr_build_octree", "hydro_godunov_level", "hydro_courant", "reflux_level"):
+        assert name in exported, name
+        assert name in _declared(), name
+
+
 def test_library_loads_and_binding_covers_header(built):
     from paper_2411_14631_gb300 import abi
     L = abi.lib()

@@ -92,7 +92,15 @@ typedef struct {
    surrogate (AMR_RIEMANN_MLP) or whose Newton solve it seeded (AMR_RIEMANN_MLP_SEEDED),
    [1] faces where the surrogate's answer was not used (fallback to a cold Newton start),
    [2] Newton iterations and [3] Newton solves made by the tile kernel's exact solver
-   and by both surrogate modes (the z-column kernel does not count). */
+   and by both surrogate modes (the z-column kernels do not count);
+   col_kernel: the z-column kernel of the deepest complete level (and of box batches whose
+   boxes are multiples of 16 cells): 0 = the library's choice (now 1), 1 = 8 x 8-cell footprints
+   marched two planes per step, 2 = 16 x 16-cell footprints with one thread per column
+   (FP32 path only, levels and boxes that are multiples of 16 cells; otherwise 1 is used);
+   col_seg: cells of z a CTA marches (0 = the library's choice; even; kernel 1 needs a
+   power of two that divides the level, kernel 2 takes any even length, the last segment
+   of the column being shorter).  Neither changes a result bit (tested): both are launch
+   shapes for the autotuner. */
 typedef struct {
     double gamma, cfl, rho_floor, p_floor;
     int32_t riemann, precision, tile, tiles_only;
@@ -101,6 +109,7 @@ typedef struct {
     int32_t limiter;
     int32_t *d_status;
     unsigned long long *d_counters;
+    int32_t col_kernel, col_seg;
 } hydro_params;
 
 /* The octree: host metadata plus non-owning views into the caller's tree memory.

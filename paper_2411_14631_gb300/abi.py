@@ -39,7 +39,8 @@ class HydroParams(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("rho_floor", C.c_double), ("p_floor", C.c_double),
                 ("riemann", C.c_int32), ("precision", C.c_int32), ("tile", C.c_int32), ("tiles_only", C.c_int32),
                 ("mlp_weights", C.c_void_p), ("mlp_resid_tol", C.c_float), ("limiter", C.c_int32),
-                ("d_status", C.c_void_p), ("d_counters", C.c_void_p)]
+                ("d_status", C.c_void_p), ("d_counters", C.c_void_p), ("col_kernel", C.c_int32),
+                ("col_seg", C.c_int32)]
 
 
 class AmrTree(C.Structure):

@@ -90,20 +90,15 @@ template <typename R, int DIR, int PXY>
 __device__ __forceinline__ void col_face(const R (*QL)[PXY], const R (*QR)[PXY], int pl, int pr_, const Prm<R> &pr,
                                          R WL[NV], R WR[NV])
 {
-    constexpr int N0 = DIR + 1, T1 = DIR == 0 ? 2 : 1, T2 = DIR == 2 ? 2 : 3;
     constexpr int S = NV + NV * DIR;
-    WL[0] = QL[0][pl] + R(0.5) * QL[S + 0][pl];
-    WR[0] = QR[0][pr_] - R(0.5) * QR[S + 0][pr_];
-    WL[1] = QL[N0][pl] + R(0.5) * QL[S + N0][pl];
-    WR[1] = QR[N0][pr_] - R(0.5) * QR[S + N0][pr_];
-    WL[2] = QL[T1][pl] + R(0.5) * QL[S + T1][pl];
-    WR[2] = QR[T1][pr_] - R(0.5) * QR[S + T1][pr_];
-    WL[3] = QL[T2][pl] + R(0.5) * QL[S + T2][pl];
-    WR[3] = QR[T2][pr_] - R(0.5) * QR[S + T2][pr_];
-    WL[4] = QL[4][pl] + R(0.5) * QL[S + 4][pl];
-    WR[4] = QR[4][pr_] - R(0.5) * QR[S + 4][pr_];
-    WL[0] = rmax(WL[0], pr.rho_floor); WR[0] = rmax(WR[0], pr.rho_floor);
-    WL[4] = rmax(WL[4], pr.p_floor); WR[4] = rmax(WR[4], pr.p_floor);
+    R tL[NV], dL[NV], tR[NV], dR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        tL[v] = QL[v][pl]; dL[v] = QL[S + v][pl];
+        tR[v] = QR[v][pr_]; dR[v] = QR[S + v][pr_];
+    }
+    face_state<DIR>(tL, dL, R(0.5), pr, WL);
+    face_state<DIR>(tR, dR, R(-0.5), pr, WR);
 }
 
 template <int DIR, typename R, int N>
@@ -256,14 +251,8 @@ __global__ void __launch_bounds__(256) k_godunov_col(ColArgs a)
                     Dl[1][v] = minmod(Wc[v] - sm.W[s0][v][si - SX], sm.W[s0][v][si + SX] - Wc[v]);
                     Dl[2][v] = minmod(Wc[v] - sm.W[sm1][v][si], sm.W[sp1][v][si] - Wc[v]);
                 }
-                const R rr = Wc[0], u = Wc[1], vv = Wc[2], w = Wc[3], pp = Wc[4];
                 R Wt[NV];
-                Wt[0] = rr - hl * (u * Dl[0][0] + rr * Dl[0][1] + vv * Dl[1][0] + rr * Dl[1][2] + w * Dl[2][0] + rr * Dl[2][3]);
-                const R ir = R(1) / rr;
-                Wt[1] = u - hl * (u * Dl[0][1] + vv * Dl[1][1] + w * Dl[2][1] + Dl[0][4] * ir);
-                Wt[2] = vv - hl * (u * Dl[0][2] + vv * Dl[1][2] + w * Dl[2][2] + Dl[1][4] * ir);
-                Wt[3] = w - hl * (u * Dl[0][3] + vv * Dl[1][3] + w * Dl[2][3] + Dl[2][4] * ir);
-                Wt[4] = pp - hl * (u * Dl[0][4] + vv * Dl[1][4] + w * Dl[2][4] + pr.gamma * pp * (Dl[0][1] + Dl[1][2] + Dl[2][3]));
+                muscl_predict(Wc, Dl, hl, pr.gamma, Wt);
                 R (*Qs)[QC] = Qp(qs);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) Qs[v][qi] = Wt[v];
@@ -497,6 +486,8 @@ amr_status launch_col(const amr_tree *t, const hydro_params *p, const double *u_
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         a.zc = a.n < 64 ? int(a.n) : 64;
         while (a.zc > 16 && (a.n / FX) * (a.n / FY) * (a.n / a.zc) < int64_t(8) * nsm) a.zc /= 2;
+        const int want = p->col_seg;
+        if (want >= 2 && want <= a.n && (want & (want - 1)) == 0) a.zc = want;
         a.work = (a.n / FX) * (a.n / FY) * (a.n / a.zc);
     }
     a.u_old = u_old; a.u_new = u_new; a.dt = dt; a.dt_next = dt_next;

@@ -15,6 +15,7 @@
 #include "hydro_math.cuh"
 #include "mlp_warp.cuh"
 #include "godunov_col.cuh"
+#include "godunov_pen.cuh"
 
 namespace amr {
 
@@ -121,18 +122,6 @@ __global__ void __launch_bounds__(256) k_ghost(TreeView tv, const double *__rest
     for (int v = 0; v < NV; ++v) out[v * stride + i] = Uw[v];
 }
 
-// cons -> prim from conserved values already in the working precision
-template <typename R>
-__device__ __forceinline__ void cons_to_prim_w(const R U[NV], const Prm<R> &p, R W[NV])
-{
-    const R rho = rmax(U[0], p.rho_floor), irho = R(1) / rho;
-    const R u = U[1] * irho, v = U[2] * irho, w = U[3] * irho;
-    const R ek = R(0.5) * rho * (u * u + v * v + w * w);
-    const R pr = (p.gamma - R(1)) * (U[4] - ek);
-    W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
-    W[4] = rmax(pr, p.p_floor);
-}
-
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
 
@@ -162,20 +151,15 @@ __device__ __forceinline__ void face_states(const Smem<R, D, RS> &sm, int r0, co
     const int Lz = DIR == 2 ? fa : 1 + t2;
     const int pl = Lx + G::P * (Ly + G::P * Lz);
     const int pR = pl + (DIR == 0 ? 1 : DIR == 1 ? G::P : G::P * G::P);
-    constexpr int N0 = DIR + 1, T1 = DIR == 0 ? 2 : 1, T2 = DIR == 2 ? 2 : 3;
     constexpr int S = NV + NV * DIR;
-    WL[0] = sm.Q[0][pl] + R(0.5) * sm.Q[S + 0][pl];
-    WR[0] = sm.Q[0][pR] - R(0.5) * sm.Q[S + 0][pR];
-    WL[1] = sm.Q[N0][pl] + R(0.5) * sm.Q[S + N0][pl];
-    WR[1] = sm.Q[N0][pR] - R(0.5) * sm.Q[S + N0][pR];
-    WL[2] = sm.Q[T1][pl] + R(0.5) * sm.Q[S + T1][pl];
-    WR[2] = sm.Q[T1][pR] - R(0.5) * sm.Q[S + T1][pR];
-    WL[3] = sm.Q[T2][pl] + R(0.5) * sm.Q[S + T2][pl];
-    WR[3] = sm.Q[T2][pR] - R(0.5) * sm.Q[S + T2][pR];
-    WL[4] = sm.Q[4][pl] + R(0.5) * sm.Q[S + 4][pl];
-    WR[4] = sm.Q[4][pR] - R(0.5) * sm.Q[S + 4][pR];
-    WL[0] = rmax(WL[0], pr.rho_floor); WR[0] = rmax(WR[0], pr.rho_floor);
-    WL[4] = rmax(WL[4], pr.p_floor); WR[4] = rmax(WR[4], pr.p_floor);
+    R tL[NV], dL[NV], tR[NV], dR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        tL[v] = sm.Q[v][pl]; dL[v] = sm.Q[S + v][pl];
+        tR[v] = sm.Q[v][pR]; dR[v] = sm.Q[S + v][pR];
+    }
+    face_state<DIR>(tL, dL, R(0.5), pr, WL);
+    face_state<DIR>(tR, dR, R(-0.5), pr, WR);
 }
 
 template <typename R, int D, int RS, int DIR>
@@ -194,18 +178,16 @@ __device__ __forceinline__ void face_flux(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>
     constexpr int N0 = DIR + 1, T1 = DIR == 0 ? 2 : 1, T2 = DIR == 2 ? 2 : 3;   // normal, transverse
     constexpr int S = NV + NV * DIR;                                             // slopes along DIR
     R WL[NV], WR[NV];
-    WL[0] = sm.Q[0][pl] + R(0.5) * sm.Q[S + 0][pl];
-    WR[0] = sm.Q[0][pR] - R(0.5) * sm.Q[S + 0][pR];
-    WL[1] = sm.Q[N0][pl] + R(0.5) * sm.Q[S + N0][pl];
-    WR[1] = sm.Q[N0][pR] - R(0.5) * sm.Q[S + N0][pR];
-    WL[2] = sm.Q[T1][pl] + R(0.5) * sm.Q[S + T1][pl];
-    WR[2] = sm.Q[T1][pR] - R(0.5) * sm.Q[S + T1][pR];
-    WL[3] = sm.Q[T2][pl] + R(0.5) * sm.Q[S + T2][pl];
-    WR[3] = sm.Q[T2][pR] - R(0.5) * sm.Q[S + T2][pR];
-    WL[4] = sm.Q[4][pl] + R(0.5) * sm.Q[S + 4][pl];
-    WR[4] = sm.Q[4][pR] - R(0.5) * sm.Q[S + 4][pR];
-    WL[0] = rmax(WL[0], pr.rho_floor); WR[0] = rmax(WR[0], pr.rho_floor);
-    WL[4] = rmax(WL[4], pr.p_floor); WR[4] = rmax(WR[4], pr.p_floor);
+    {
+        R tL[NV], dL[NV], tR[NV], dR[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            tL[v] = sm.Q[v][pl]; dL[v] = sm.Q[S + v][pl];
+            tR[v] = sm.Q[v][pR]; dR[v] = sm.Q[S + v][pR];
+        }
+        face_state<DIR>(tL, dL, R(0.5), pr, WL);
+        face_state<DIR>(tR, dR, R(-0.5), pr, WR);
+    }
     if (a.harvest) {
         // deterministic sample of the faces (hash of tile, direction and face)
         uint64_t h = (uint64_t(tile) * 3 + DIR) * 0x9E3779B97F4A7C15ull + uint64_t(r0) * 0xBF58476D1CE4E5B9ull;
@@ -458,14 +440,8 @@ __global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
                     Dl[d][v] = slope(pr, Wc[v] - sm.W[v][si - st[d]], sm.W[v][si + st[d]] - Wc[v]);
-            const R r = Wc[0], u = Wc[1], vv = Wc[2], w = Wc[3], pp = Wc[4];
             R Wt[NV];
-            Wt[0] = r - hl * (u * Dl[0][0] + r * Dl[0][1] + vv * Dl[1][0] + r * Dl[1][2] + w * Dl[2][0] + r * Dl[2][3]);
-            const R ir = R(1) / r;
-            Wt[1] = u - hl * (u * Dl[0][1] + vv * Dl[1][1] + w * Dl[2][1] + Dl[0][4] * ir);
-            Wt[2] = vv - hl * (u * Dl[0][2] + vv * Dl[1][2] + w * Dl[2][2] + Dl[1][4] * ir);
-            Wt[3] = w - hl * (u * Dl[0][3] + vv * Dl[1][3] + w * Dl[2][3] + Dl[2][4] * ir);
-            Wt[4] = pp - hl * (u * Dl[0][4] + vv * Dl[1][4] + w * Dl[2][4] + pr.gamma * pp * (Dl[0][1] + Dl[1][2] + Dl[2][3]));
+            muscl_predict(Wc, Dl, hl, pr.gamma, Wt);
 #pragma unroll
             for (int v = 0; v < NV; ++v) sm.Q[v][p] = Wt[v];
 #pragma unroll
@@ -620,6 +596,24 @@ static amr_status launch(const GArgs &a, int64_t ntile, cudaStream_t st)
     return AMR_OK;
 }
 
+// The z-column kernel for the deepest complete level (or the box batch): the pencil
+// kernel (16 x 16 footprints, FP32) when asked for and applicable, else the slab kernel
+// (8 x 8 footprints).
+template <typename R>
+amr_status launch_column(const amr_tree *t, const hydro_params *p, const double *u_old, double *u_new,
+                         const double *dt, double *dt_next, cudaStream_t st)
+{
+    const bool exact = p->riemann == AMR_RIEMANN_EXACT;
+    if constexpr (sizeof(R) == 4) {
+        const bool fits = t->n_inst > 0 ? (t->col_work > 0 && t->col_work % 4 == 0) : (t->grid_level >= 4);
+        if (p->col_kernel == 2 && fits)
+            return exact ? launch_pen<AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, p->col_seg, st)
+                         : launch_pen<AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, p->col_seg, st);
+    }
+    return exact ? launch_col<R, AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, st)
+                 : launch_col<R, AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, st);
+}
+
 // Launch the kernel(s) of precision R for one level or for all levels (level = -1).
 // Levels whose tiles of the requested depth would be rooted above level 1 use depth 1.
 template <typename R>
@@ -636,10 +630,7 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
         // batch mode: every box in one launch (z-column kernel when every box is a multiple of
         // 16 cells, else tiles)
         if (level != -1) return AMR_EINVAL;
-        if (col_ok && t->col_work > 0)
-            return p->riemann == AMR_RIEMANN_EXACT
-                       ? launch_col<R, AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, st)
-                       : launch_col<R, AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, st);
+        if (col_ok && t->col_work > 0) return launch_column<R>(t, p, u_old, u_new, dt, dt_next, st);
         if (depth == 2 && t->tile_off[1][1] == 0) depth = 1;            // some box is not a multiple of 8
         if (mlp_like) depth = 1;
         const int d = depth;
@@ -681,9 +672,7 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
     // the deepest complete level goes to the z-column kernel (bitwise the same per cell);
     // the levels above it to the tile kernel
     if (col_ok && t->grid && gl >= 3 && gl >= l0 && gl <= l1) {
-        const amr_status r = p->riemann == AMR_RIEMANN_EXACT
-                                 ? launch_col<R, AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, st)
-                                 : launch_col<R, AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, st);
+        const amr_status r = launch_column<R>(t, p, u_old, u_new, dt, dt_next, st);
         if (r != AMR_OK) return r;
         // levels below a complete level have no leaf cells: nothing of theirs survives the
         // restriction, so they are not updated

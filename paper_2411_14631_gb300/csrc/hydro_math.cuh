@@ -68,6 +68,19 @@ template <> __device__ __forceinline__ float to_work<float>(double x) { return d
 __device__ __forceinline__ double to_state(double x) { return x; }
 __device__ __forceinline__ double to_state(float x) { return f2d_bits(x); }
 
+// Products and multiply-adds written out.  Left to itself the compiler fuses a*b + c*d
+// into either fma(a, b, c*d) or fma(c, d, a*b), and the choice can differ between kernels
+// that inline the same code; these pin one rounding sequence, so that every kernel that
+// uses the functions below computes the same bits.  mulr is a multiplication the compiler
+// never fuses; fmar a fused multiply-add.
+__device__ __forceinline__ float mulr(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mulr(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fmar(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmar(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// u^2 + v^2 + w^2, accumulated left to right
+template <typename R> __device__ __forceinline__ R sq3(R u, R v, R w) { return fmar(w, w, fmar(v, v, mulr(u, u))); }
+
 template <typename R> struct Prm {
     R gamma, rho_floor, p_floor;
     int limiter = AMR_LIMITER_MINMOD;   // slopes of the reconstruction
@@ -97,16 +110,26 @@ template <typename R> __device__ __forceinline__ R slope(const Prm<R> &p, R a, R
     return p.limiter == AMR_LIMITER_MC ? mc_limit(a, b) : minmod(a, b);
 }
 
+// cons -> prim from conserved values already in the working precision
+template <typename R>
+__device__ __forceinline__ void cons_to_prim_w(const R U[NV], const Prm<R> &p, R W[NV])
+{
+    const R rho = rmax(U[0], p.rho_floor), irho = R(1) / rho;
+    const R u = mulr(U[1], irho), v = mulr(U[2], irho), w = mulr(U[3], irho);
+    const R ek = mulr(mulr(R(0.5), rho), sq3(u, v, w));
+    const R pr = mulr(p.gamma - R(1), U[4] - ek);
+    W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
+    W[4] = rmax(pr, p.p_floor);
+}
+
 // conserved (FP64 storage) -> primitive in precision R, floors applied
 template <typename R>
 __device__ __forceinline__ void cons_to_prim(const double U[NV], const Prm<R> &p, R W[NV])
 {
-    const R rho = rmax(to_work<R>(U[0]), p.rho_floor), irho = R(1) / rho;
-    const R u = to_work<R>(U[1]) * irho, v = to_work<R>(U[2]) * irho, w = to_work<R>(U[3]) * irho;
-    const R ek = R(0.5) * rho * (u * u + v * v + w * w);
-    const R pr = (p.gamma - R(1)) * (to_work<R>(U[4]) - ek);
-    W[0] = rho; W[1] = u; W[2] = v; W[3] = w;
-    W[4] = rmax(pr, p.p_floor);
+    R Uw[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Uw[v] = to_work<R>(U[v]);
+    cons_to_prim_w(Uw, p, W);
 }
 
 // physical flux through a face whose normal is the first velocity component
@@ -114,13 +137,14 @@ template <typename R>
 __device__ __forceinline__ void flux_normal(const R W[NV], R g, R F[NV], R U[NV])
 {
     const R rho = W[0], u = W[1], v = W[2], w = W[3], pr = W[4];
-    const R E = pr / (g - R(1)) + R(0.5) * rho * (u * u + v * v + w * w);
-    F[0] = rho * u;
-    F[1] = rho * u * u + pr;
-    F[2] = rho * u * v;
-    F[3] = rho * u * w;
-    F[4] = u * (E + pr);
-    U[0] = rho; U[1] = rho * u; U[2] = rho * v; U[3] = rho * w; U[4] = E;
+    const R E = fmar(mulr(R(0.5), rho), sq3(u, v, w), pr / (g - R(1)));
+    const R ru = mulr(rho, u);
+    F[0] = ru;
+    F[1] = fmar(ru, u, pr);
+    F[2] = mulr(ru, v);
+    F[3] = mulr(ru, w);
+    F[4] = mulr(u, E + pr);
+    U[0] = rho; U[1] = ru; U[2] = mulr(rho, v); U[3] = mulr(rho, w); U[4] = E;
 }
 
 // HLLC flux (Toro, Spruce & Speares 1994); the side used is chosen before computing,
@@ -130,11 +154,11 @@ __device__ __forceinline__ void hllc(const R WL[NV], const R WR[NV], R g, R F[NV
 {
     const R rL = WL[0], uL = WL[1], pL = WL[4];
     const R rR = WR[0], uR = WR[1], pR = WR[4];
-    const R cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+    const R cL = sqrt(mulr(g, pL) / rL), cR = sqrt(mulr(g, pR) / rR);
     const R SL = fmin(uL - cL, uR - cR);
     const R SR = fmax(uL + cL, uR + cR);
-    const R mL = rL * (SL - uL), mR = rR * (SR - uR);   // mass fluxes through the outer waves
-    const R Ss = (pR - pL + uL * mL - uR * mR) / (mL - mR);
+    const R mL = mulr(rL, SL - uL), mR = mulr(rR, SR - uR);   // mass fluxes through the outer waves
+    const R Ss = fmar(-uR, mR, fmar(uL, mL, pR - pL)) / (mL - mR);
     const bool left = (SL >= R(0)) || (Ss >= R(0));
     const bool star = !(SL >= R(0)) && (Ss >= R(0) || SR > R(0));
     R WK[NV];
@@ -149,11 +173,11 @@ __device__ __forceinline__ void hllc(const R WL[NV], const R WR[NV], R g, R F[NV
         // d ((S_K - u_K) E_K + (S* - u_K) p_K) + f (S* - u_K) S*, one division in all
         const R rK = WK[0], uK = WK[1], pK = WK[4];
         const R d = R(1) / (SK - Ss);
-        const R f = rK * (SK - uK) * d;
-        const R Us[NV] = {f, f * Ss, f * WK[2], f * WK[3],
-                          d * ((SK - uK) * UK[4] + (Ss - uK) * pK) + f * (Ss - uK) * Ss};
+        const R f = mulr(mulr(rK, SK - uK), d);
+        const R Us[NV] = {f, mulr(f, Ss), mulr(f, WK[2]), mulr(f, WK[3]),
+                          fmar(mulr(f, Ss - uK), Ss, mulr(d, fmar(Ss - uK, pK, mulr(SK - uK, UK[4]))))};
 #pragma unroll
-        for (int v = 0; v < NV; ++v) F[v] = FK[v] + SK * (Us[v] - UK[v]);
+        for (int v = 0; v < NV; ++v) F[v] = fmar(SK, Us[v] - UK[v], FK[v]);
     } else {
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = FK[v];
@@ -192,7 +216,7 @@ __device__ int exact_star(const R WL[NV], const R WR[NV], R g, R tol, int maxit,
     const R du = uR - uL;
     if (R(2) * (cL + cR) / (g - R(1)) <= du) return AMR_ENONPHYSICAL;
     const R eps = sizeof(R) == 8 ? R(1e-300) : R(1e-37);
-    R p = p0 > R(0) ? p0 : R(0.5) * (pL + pR) - R(0.125) * du * (rL + rR) * (cL + cR);
+    R p = p0 > R(0) ? p0 : mulr(R(0.5), pL + pR) - mulr(mulr(mulr(R(0.125), du), rL + rR), cL + cR);
     if (p < eps) p = eps;
     int it;
     for (it = 1; it <= maxit; ++it) {
@@ -209,7 +233,7 @@ __device__ int exact_star(const R WL[NV], const R WR[NV], R g, R tol, int maxit,
     side_f(p, rL, pL, cL, g, fL, dfL);
     side_f(p, rR, pR, cR, g, fR, dfR);
     ps = p;
-    us = R(0.5) * (uL + uR) + R(0.5) * (fR - fL);
+    us = mulr(R(0.5), uL + uR) + mulr(R(0.5), fR - fL);
     if (iters) *iters = it > maxit ? maxit : it;
     return it > maxit ? AMR_ENOCONV : 0;
 }
@@ -269,6 +293,43 @@ __device__ void exact_sample0(const R WL[NV], const R WR[NV], R g, R ps, R us, R
         }
     }
     W[0] = rho; W[1] = u; W[2] = lside ? WL[2] : WR[2]; W[3] = lside ? WL[3] : WR[3]; W[4] = p;
+}
+
+// MUSCL-Hancock half step in primitive variables (Toro Sec. 14.4) of a cell from its
+// primitives Wc and undivided slopes Dl[d] (hl = dt / (2 dx)); every term's products
+// accumulated left to right
+template <typename R>
+__device__ __forceinline__ void muscl_predict(const R Wc[NV], const R Dl[3][NV], R hl, R gamma, R Wt[NV])
+{
+    const R rr = Wc[0], u = Wc[1], vv = Wc[2], w = Wc[3], pp = Wc[4];
+    R s = fmar(rr, Dl[2][3], fmar(w, Dl[2][0], fmar(rr, Dl[1][2], fmar(vv, Dl[1][0], fmar(rr, Dl[0][1],
+                                                                                        mulr(u, Dl[0][0]))))));
+    Wt[0] = fmar(-hl, s, rr);
+    const R ir = R(1) / rr;
+    s = fmar(Dl[0][4], ir, fmar(w, Dl[2][1], fmar(vv, Dl[1][1], mulr(u, Dl[0][1]))));
+    Wt[1] = fmar(-hl, s, u);
+    s = fmar(Dl[1][4], ir, fmar(w, Dl[2][2], fmar(vv, Dl[1][2], mulr(u, Dl[0][2]))));
+    Wt[2] = fmar(-hl, s, vv);
+    s = fmar(Dl[2][4], ir, fmar(w, Dl[2][3], fmar(vv, Dl[1][3], mulr(u, Dl[0][3]))));
+    Wt[3] = fmar(-hl, s, w);
+    s = fmar(mulr(gamma, pp), (Dl[0][1] + Dl[1][2]) + Dl[2][3], fmar(w, Dl[2][4], fmar(vv, Dl[1][4],
+                                                                                      mulr(u, Dl[0][4]))));
+    Wt[4] = fmar(-hl, s, pp);
+}
+
+// face state of a predicted cell, W~ + half Delta_D (half = +1/2: the cell is the face's
+// left state; -1/2: its right state), in the face-normal frame of direction D (density,
+// normal velocity, the two transverse velocities in axis order, pressure), density and
+// pressure floored
+template <int D, typename R>
+__device__ __forceinline__ void face_state(const R Wt[NV], const R DlD[NV], R half, const Prm<R> &pr, R S[NV])
+{
+    constexpr int N0 = D + 1, T1 = D == 0 ? 2 : 1, T2 = D == 2 ? 2 : 3;
+    S[0] = rmax(fmar(half, DlD[0], Wt[0]), pr.rho_floor);
+    S[1] = fmar(half, DlD[N0], Wt[N0]);
+    S[2] = fmar(half, DlD[T1], Wt[T1]);
+    S[3] = fmar(half, DlD[T2], Wt[T2]);
+    S[4] = rmax(fmar(half, DlD[4], Wt[4]), pr.p_floor);
 }
 
 // dt candidate of one cell: cfl * dx / sum_d (|u_d| + c), from the FP64 state; p, cfl and

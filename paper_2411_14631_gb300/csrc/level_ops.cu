@@ -199,6 +199,7 @@ static amr_status check(const amr_tree *t, const hydro_params *p)
     if (p->precision != AMR_PREC_FP64 && p->precision != AMR_PREC_FP32) return AMR_EINVAL;
     if (p->tile < 0 || p->tile > 2) return AMR_EINVAL;
     if (p->limiter != AMR_LIMITER_MINMOD && p->limiter != AMR_LIMITER_MC) return AMR_EINVAL;
+    if (p->col_kernel < 0 || p->col_kernel > 2 || p->col_seg < 0 || (p->col_seg & 1)) return AMR_EINVAL;
     return AMR_OK;
 }
 

@@ -140,11 +140,12 @@ class Params:
     """hydro_params with device status word and counters."""
 
     def __init__(self, gamma, cfl=0.8, rho_floor=1e-10, p_floor=1e-20, riemann=abi.RIEMANN_HLLC,
-                 precision=abi.PREC_FP64, tile=0, device="cuda:0", tiles_only=False, limiter=abi.LIMITER_MINMOD):
+                 precision=abi.PREC_FP64, tile=0, device="cuda:0", tiles_only=False, limiter=abi.LIMITER_MINMOD,
+                 col_kernel=0, col_seg=0):
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
         self.counters = torch.zeros(abi.NCOUNTERS, dtype=torch.int64, device=device)
         self.c = abi.HydroParams(gamma, cfl, rho_floor, p_floor, riemann, precision, tile, int(tiles_only), None,
-                                 0.0, limiter, self.status.data_ptr(), self.counters.data_ptr())
+                                 0.0, limiter, self.status.data_ptr(), self.counters.data_ptr(), col_kernel, col_seg)
 
     def read_status(self):
         s = C.c_int32()

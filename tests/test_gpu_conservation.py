@@ -103,7 +103,10 @@ def test_argument_errors(H):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_step_conserves_measured_on_gpu(H, precision):
     """Ten steps on a periodic AMR tree keep the leaf totals of mass, momentum and energy
-    to rounding (FP64 accumulation in both paths), as measured by hydro_conservation."""
+    to rounding, as measured by hydro_conservation: FP64 round-off in the FP64 path; in
+    the FP32 path a cell's six face fluxes are summed in FP32 before the FP64 update, so
+    the totals keep FP32 round-off of the increments (the bound of the other
+    conservation test, 1e-9 after ten steps)."""
     from paper_2411_14631_gb300.bench_util import cell_centres_of
     lx = W.random_tree(3, 2, 17, p_refine=0.3, periodic=True)
     g = H.Octree(lx, 3, (0,) * 6)
@@ -120,5 +123,6 @@ def test_step_conserves_measured_on_gpu(H, precision):
         sim.step()
     t1 = H.hydro_conservation(g, sim.u).cpu().numpy()[0]
     scale = np.maximum(t0[1], t1[1])
-    assert np.all(np.abs(t1[0] - t0[0]) <= 1e-13 * 10 * scale), (t0, t1)
+    tol = 1e-13 * 10 if precision == 0 else 1e-9
+    assert np.all(np.abs(t1[0] - t0[0]) <= tol * scale), (t0, t1)
     assert sim.prm.read_status()[0] == 0

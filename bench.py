@@ -495,19 +495,19 @@ def study_sedov(args):
     out = {"study": "Sedov-Taylor batch: 48 boxes, one launch per step, per-box CFL", "data": "synthetic",
            "sizes": [int(x) for x in sizes], "cells": cells}
     from paper_2411_14631_gb300 import autotune
-    tile, tune_ms = autotune.tune(tree, 1.4, w0, precision=abi.PREC_FP32, cfl=CFL, use_cache=False)
+    shape, tune_ms = autotune.tune(tree, 1.4, w0, precision=abi.PREC_FP32, cfl=CFL, use_cache=False)
     res = {}
     for name, prec, steps in (("fp32_chosen", abi.PREC_FP32, args.steps), ("fp64_plain", abi.PREC_FP64, 3)):
-        prm = H.Params(1.4, cfl=CFL, precision=prec, tile=tile if prec == abi.PREC_FP32 else 1)
+        prm = H.Params(1.4, cfl=CFL, precision=prec, **(shape if prec == abi.PREC_FP32 else dict(tile=1)))
         ms, _ = time_graph(H, tree, prm, w0, steps, 2)
         res[name] = {"ms_per_step": ms, "cell_updates_per_s": cells / (ms * 1e-3), "steps_timed": steps}
     res["speedup"] = res["fp64_plain"]["ms_per_step"] / res["fp32_chosen"]["ms_per_step"]
     out["throughput"] = res
-    out["tile_depth"] = tile
+    out["launch_shape"] = shape
     out["autotune_ms_per_step"] = tune_ms
     # accuracy run: FP32 chosen path, each box frozen at its own target radius
     xi0 = 0.851 ** -0.2
-    prm = H.Params(1.4, cfl=CFL, precision=abi.PREC_FP32, tile=tile)
+    prm = H.Params(1.4, cfl=CFL, precision=abi.PREC_FP32, **shape)
     sim = H.Simulation(tree, prm, w0=w0)
     tb = np.zeros(len(sizes))
     frozen = np.zeros(len(sizes), dtype=bool)
@@ -574,17 +574,17 @@ def study_amr(args):
            "leaf_cells_per_level": {int(l): int((leaf & (lvl == l)).sum()) for l in range(7, 13)},
            "setup_seconds": time.perf_counter() - t0}
     from paper_2411_14631_gb300 import autotune
-    tile, tune_ms = autotune.tune(tree, 5.0 / 3.0, w0, precision=abi.PREC_FP32, cfl=CFL, use_cache=False)
+    shape, tune_ms = autotune.tune(tree, 5.0 / 3.0, w0, precision=abi.PREC_FP32, cfl=CFL, use_cache=False)
     res = {}
     for name, prec, steps in (("fp32_chosen", abi.PREC_FP32, args.steps), ("fp64_plain", abi.PREC_FP64, 3)):
-        prm = H.Params(5.0 / 3.0, cfl=CFL, precision=prec, tile=tile if prec == abi.PREC_FP32 else 1)
+        prm = H.Params(5.0 / 3.0, cfl=CFL, precision=prec, **(shape if prec == abi.PREC_FP32 else dict(tile=1)))
         ms, sim = time_graph(H, tree, prm, w0, steps, 2)
         res[name] = {"ms_per_step": ms, "cell_updates_per_s": int(leaf.sum()) / (ms * 1e-3), "steps_timed": steps}
     res["speedup"] = res["fp64_plain"]["ms_per_step"] / res["fp32_chosen"]["ms_per_step"]
     out["throughput"] = res
     # sub-cycled levels (level l makes 2^(l-7) steps per coarse step): simulated time per
     # wall-clock second against one time step for all levels, FP32 path, CUDA graphs
-    prm32 = H.Params(5.0 / 3.0, cfl=CFL, precision=abi.PREC_FP32, tile=tile)
+    prm32 = H.Params(5.0 / 3.0, cfl=CFL, precision=abi.PREC_FP32, **shape)
     single = H.Simulation(tree, prm32, w0=w0)
     dt_single = float(single.dt.item())
     del single
@@ -611,11 +611,12 @@ def study_amr(args):
     out["subcycled"]["gain_in_sim_time_per_wall_s"] = (out["subcycled"]["sim_time_per_wall_s"] /
                                                        out["subcycled"]["sim_time_per_wall_s_single_dt"])
     del sc
-    out["tile_depth"] = tile
+    out["launch_shape"] = shape
     out["autotune_ms_per_step"] = tune_ms
     vol = np.ldexp(1.0, -3 * lvl.astype(np.int64))[leaf]
     for name, prec in (("fp64", abi.PREC_FP64), ("fp32", abi.PREC_FP32)):
-        sim = H.Simulation(tree, H.Params(5.0 / 3.0, cfl=CFL, precision=prec, tile=tile if prec else 1), w0=w0)
+        sim = H.Simulation(tree, H.Params(5.0 / 3.0, cfl=CFL, precision=prec, **(shape if prec else dict(tile=1))),
+                           w0=w0)
         u0 = sim.u.cpu().numpy()
         tot0 = np.array([np.sum(u0[v, leaf] * vol) for v in range(5)])
         for _ in range(10):
@@ -806,12 +807,12 @@ def main():
     w0 = prims_for(xyz, rho, v)
     leaf = tree.leaf_cells()
 
-    tile = args.tile
+    shape = dict(tile=args.tile, col_kernel=0, col_seg=0)
     tune_ms = None
-    if tile == 0:
+    if args.tile == 0:
         from paper_2411_14631_gb300 import autotune
-        tile, tune_ms = autotune.tune(tree, GAMMA, w0, precision=abi.PREC_FP32, cfl=CFL)
-    prm32 = H.Params(GAMMA, cfl=CFL, precision=abi.PREC_FP32, tile=tile, device=dev)
+        shape, tune_ms = autotune.tune(tree, GAMMA, w0, precision=abi.PREC_FP32, cfl=CFL)
+    prm32 = H.Params(GAMMA, cfl=CFL, precision=abi.PREC_FP32, device=dev, **shape)
     clk = Clocks(local)
 
     def barrier():
@@ -843,7 +844,7 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "leaf_cells": leaf, "octs": tree.noct,
                       "precision": "FP32 reconstruction + Riemann, FP64 state accumulation",
-                      "tile_depth": tile, "autotune_ms_per_step": tune_ms, "cuda_graph": True,
+                      "launch_shape": shape, "autotune_ms_per_step": tune_ms, "cuda_graph": True,
                       "parallelism": "replicas" if ws > 1 else "single GPU",
                       "l2": "inputs larger than L2 (two 671 MB FP64 state arrays)"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

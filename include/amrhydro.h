@@ -94,7 +94,7 @@ typedef struct {
    [2] Newton iterations and [3] Newton solves made by the tile kernel's exact solver
    and by both surrogate modes (the z-column kernels do not count);
    col_kernel: the z-column kernel of the deepest complete level (and of box batches whose
-   boxes are multiples of 16 cells): 0 = the library's choice (now 1), 1 = 8 x 8-cell footprints
+   boxes are multiples of 16 cells): 0 = the library's choice (2 where it applies), 1 = 8 x 8-cell footprints
    marched two planes per step, 2 = 16 x 16-cell footprints with one thread per column
    (FP32 path only, levels and boxes that are multiples of 16 cells; otherwise 1 is used);
    col_seg: cells of z a CTA marches (0 = the library's choice; even; kernel 1 needs a
@@ -208,6 +208,8 @@ amr_status hydro_godunov_level(const amr_tree *tree, int level, const hydro_para
                                const double *d_u_old, double *d_u_new, double *d_flux_reg,
                                const double *d_dt, double *d_dt_next, amr_stream stream);
 
+/* Bytes of the caller's flux-register buffer (device, 256-byte aligned): the register
+   rows and the interpolated children of the ghost fathers. */
 size_t hydro_flux_reg_bytes(const amr_tree *tree);
 
 /* Refluxing and restriction for coarse level `level` (1 <= level < levelmax): the part
@@ -232,7 +234,9 @@ amr_status reflux_level(const amr_tree *tree, int level, const hydro_params *par
 
 /* One whole step: resets *d_dt_next (if not NULL) to a large value, then godunov on
    every level (one launch), then reflux + restriction from the finest level up.
-   Equivalent to the calls above in that order. */
+   Equivalent to the calls above in that order (the same bits): below the deepest
+   complete level minus one, where every cell is refined and the step is a pure
+   restriction, three levels are restricted per launch (one CTA per subtree). */
 amr_status hydro_step(const amr_tree *tree, const hydro_params *params, const double *d_u_old,
                       double *d_u_new, double *d_flux_reg, const double *d_dt, double *d_dt_next,
                       amr_stream stream);

@@ -597,8 +597,8 @@ static amr_status launch(const GArgs &a, int64_t ntile, cudaStream_t st)
 }
 
 // The z-column kernel for the deepest complete level (or the box batch): the pencil
-// kernel (16 x 16 footprints, FP32) when asked for and applicable, else the slab kernel
-// (8 x 8 footprints).
+// kernel (16 x 16 footprints, FP32) where it applies and is not declined, else the slab
+// kernel (8 x 8 footprints).
 template <typename R>
 amr_status launch_column(const amr_tree *t, const hydro_params *p, const double *u_old, double *u_new,
                          const double *dt, double *dt_next, cudaStream_t st)
@@ -606,7 +606,7 @@ amr_status launch_column(const amr_tree *t, const hydro_params *p, const double 
     const bool exact = p->riemann == AMR_RIEMANN_EXACT;
     if constexpr (sizeof(R) == 4) {
         const bool fits = t->n_inst > 0 ? (t->col_work > 0 && t->col_work % 4 == 0) : (t->grid_level >= 4);
-        if (p->col_kernel == 2 && fits)
+        if (p->col_kernel != 1 && fits)
             return exact ? launch_pen<AMR_RIEMANN_EXACT>(t, p, u_old, u_new, dt, dt_next, p->col_seg, st)
                          : launch_pen<AMR_RIEMANN_HLLC>(t, p, u_old, u_new, dt, dt_next, p->col_seg, st);
     }

@@ -2,15 +2,16 @@
 // the z-column update.
 //
 // A CTA owns a 16 x 16-cell footprint of the level and marches a segment of its column
-// in z one cell plane at a time.  Each of the 256 interior threads owns one (x, y)
-// column; a 32-thread strip warp predicts the four one-cell strips around the footprint
-// (the left / right / bottom / top neighbours of the edge cells) and solves the faces on
-// the footprint's right and top edges.  Per plane p:
+// in z one cell plane at a time.  Each of its 256 threads owns one (x, y) column; on top
+// of that, warps 0 and 1 predict the four one-cell strips around the footprint (the
+// left / right and bottom / top neighbours of the edge cells), warp 2 solves the faces on
+// the footprint's right and top edges, and warps 3-7 gather the stencil cells beyond the
+// first 256 (each role warp-uniform).  Per plane p:
 //   A  gather of stencil plane p+2 (20 x 20 cells, FP64 -> FP32 primitives) into a ring
 //      of four planes in shared memory (loads issued first, stores last);
 //   B  slopes and MUSCL-Hancock predictor of plane p: the interior thread keeps its
 //      cell's -x, -y, +z and -z face states in registers and publishes +x and +y in
-//      shared memory; the strip warp publishes its strips' inward face states;
+//      shared memory; warps 0 and 1 publish the strips' inward face states;
 //   C  the z face below plane p from two states the thread holds (no shared memory);
 //   -- one barrier --
 //   E  FP64 update of plane p-1: its own x-left and y-left fluxes and both z fluxes come
@@ -36,7 +37,9 @@ struct PenGeo {
     static constexpr int NS = SX * SY;                // 400
     static constexpr int NI = FX * FY;                // 256 interior columns = interior threads
     static constexpr int OX = SX / 2, NO = OX * (SY / 2);   // footprint oct columns (10 x 10)
-    static constexpr int NT = NI + 32;                // + the strip warp
+    static constexpr int NT = NI;                     // one thread per column
+    static constexpr int NXG = NS - NI;               // gather items beyond the first 256 (144)
+    static constexpr int XG0 = 96;                    // first thread with one of them (warp 3)
 };
 
 template <bool FINER> struct PenSmem {
@@ -63,7 +66,7 @@ template <bool FINER> struct PenSmem {
     float Gy1[2][G::NI];
     // new states of the last three planes (slot = plane % 3), [variable][x + 16 y]
     double Ur[3][NV][G::NI];
-    int32_t oct[4][G::NO];                            // oct id per footprint oct column, slot = layer & 3
+    int32_t oct[8][G::NO];                            // oct id per footprint oct column, slot = layer & 7
     uint8_t ref[FINER ? 8 : 1][FINER ? G::NS : 1];    // refined flag per stencil cell, slot = plane & 7
 };
 
@@ -90,7 +93,7 @@ template <int D> __device__ __forceinline__ void pen_acc(float dU[NV], const flo
 }
 
 template <int RS, bool FINER>
-__global__ void __maxnreg__(112) k_godunov_pen(ColArgs a)
+__global__ void __launch_bounds__(PenGeo::NT, 2) k_godunov_pen(ColArgs a)
 {
     using G = PenGeo;
     using S = PenSmem<FINER>;
@@ -99,8 +102,8 @@ __global__ void __maxnreg__(112) k_godunov_pen(ColArgs a)
     S &sm = *reinterpret_cast<S *>(smem_raw);
     const TreeView &tv = a.tv;
     const int tid = threadIdx.x;
-    const bool strip = tid >= G::NI;
-    const int lane = tid & 31;
+    const int lane = tid & 31, wid = tid >> 5;
+    const bool xg = tid >= G::XG0 && tid < G::XG0 + G::NXG;      // has a second gather item
     const int x = lane & 15, y = 2 * (tid >> 5) + (lane >> 4);   // interior column (interior threads)
     const int ci = x + G::FX * y;                                  // its interior index
     const int sio = (x + 2) + SX * (y + 2);                        // its stencil index
@@ -160,32 +163,23 @@ __global__ void __maxnreg__(112) k_godunov_pen(ColArgs a)
         auto oct_fill = [&](int L, int o) {
             const int wx = wrap(X0 + 2 * (o % G::OX), 0), wy = wrap(Y0 + 2 * (o / G::OX), 1);
             const int32_t oi = (wx >> 1) + Mi * ((wy >> 1) + Mi * (wrap(2 * L, 2) >> 1));
-            sm.oct[L & 3][o] = batch ? obase + oi : a.grid[oi];
+            sm.oct[L & 7][o] = batch ? obase + oi : a.grid[oi];
         };
         // gather items: stencil cell q (quads of the 2 x 2 cells of one oct column, so four
         // lanes read 32 contiguous bytes of a variable): packed stencil index | oct column
-        // << 9 | x-y cell bits << 16.  Interior thread t: item t; strip lane l: 256 + l + 32 k.
+        // << 9 | x-y cell bits << 16.  Thread t: item t, and item 256 + t - 96 for t in [96, 240).
         auto gitem = [&](int q) -> int {
             const int o = q >> 2, sub = q & 3;
             const int i = 2 * (o % G::OX) + (sub & 1), j = 2 * (o / G::OX) + (sub >> 1);
             const int cb = (wrap(X0 + i, 0) & 1) + 2 * (wrap(Y0 + j, 1) & 1);
             return (i + SX * j) | (o << 9) | (cb << 16);
         };
-        constexpr int NGS = (G::NS - G::NI + 31) / 32;   // strip-warp gather items per lane (5)
-        int gpk[NGS];
-        if (!strip) {
-            gpk[0] = gitem(tid);
-        } else {
-#pragma unroll
-            for (int k = 0; k < NGS; ++k) {
-                const int q = G::NI + lane + 32 * k;
-                gpk[k] = q < G::NS ? gitem(q) : -1;
-            }
-        }
+        const int gpk0 = gitem(tid);
+        const int gpk1 = xg ? gitem(G::NI + tid - G::XG0) : 0;
         // load of gather item pk of stencil plane z (FP64 state), then conversion and store
         auto gload = [&](int pk, int z, double U[NV]) -> int32_t {
             const int o = (pk >> 9) & 127, cb = pk >> 16;
-            const int32_t cid = sm.oct[(z >> 1) & 3][o] * 8 + cb + 4 * (wrap(z, 2) & 1);
+            const int32_t cid = sm.oct[(z >> 1) & 7][o] * 8 + cb + 4 * (wrap(z, 2) & 1);
 #pragma unroll
             for (int v = 0; v < NV; ++v) U[v] = uo[v][cid];
             return cid;
@@ -199,19 +193,13 @@ __global__ void __maxnreg__(112) k_godunov_pen(ColArgs a)
             pen_st(sm.Wv[z & 3], sm.Wp[z & 3], si, Wc);
             if constexpr (FINER) sm.ref[z & 7][si] = (tv.refmask[cid >> 3] >> (cid & 7)) & 1;
         };
-        auto gather_all = [&](int z) {   // every item of this thread, one after the other
-            if (!strip) {
-                double U[NV];
-                const int32_t cid = gload(gpk[0], z, U);
-                gstore(gpk[0], z, U, cid);
-            } else {
-#pragma unroll
-                for (int k = 0; k < NGS; ++k) {
-                    if (gpk[k] < 0) continue;
-                    double U[NV];
-                    const int32_t cid = gload(gpk[k], z, U);
-                    gstore(gpk[k], z, U, cid);
-                }
+        auto gather_all = [&](int z) {   // this thread's items, one after the other
+            double U[NV];
+            int32_t cid = gload(gpk0, z, U);
+            gstore(gpk0, z, U, cid);
+            if (xg) {
+                cid = gload(gpk1, z, U);
+                gstore(gpk1, z, U, cid);
             }
         };
         // slopes + predictor of stencil cell si of plane p
@@ -236,7 +224,7 @@ __global__ void __maxnreg__(112) k_godunov_pen(ColArgs a)
         // restriction of the father of footprint oct (w & 63) of layer k, variable w >> 6
         auto restrict_item = [&](int k, int w) {
             const int v = w >> 6, o = w & 63, ox = o & 7, oy = o >> 3;
-            const int32_t oct = sm.oct[k & 3][(ox + 1) + G::OX * (oy + 1)];
+            const int32_t oct = sm.oct[k & 7][(ox + 1) + G::OX * (oy + 1)];
             if (!tv.fused[oct]) return;
             double acc = 0.0;
 #pragma unroll
@@ -246,9 +234,8 @@ __global__ void __maxnreg__(112) k_godunov_pen(ColArgs a)
         };
         auto restrict_layer = [&](int k) {
             if (batch) return;
-            if (!strip) {
-                restrict_item(k, tid);
-            } else {
+            restrict_item(k, tid);
+            if (wid == 2) {                               // the 64 items beyond the first 256
                 restrict_item(k, G::NI + lane);
                 restrict_item(k, G::NI + 32 + lane);
             }
@@ -266,24 +253,38 @@ __global__ void __maxnreg__(112) k_godunov_pen(ColArgs a)
         for (int p = z0 - 1; p <= z1; ++p) {
             const bool first = p == z0 - 1, last = p == z1, mid = !first && !last;
             const int q = p - 1;                          // plane updated in this iteration
-            const bool upd = !strip && q >= z0;
+            const bool upd = q >= z0;
             const bool gat = p + 2 <= z1 + 1;
             // old state of the cell to update, and this thread's first gather item: loads first
-            double Uo[NV], Ug[NV];
-            int32_t ucid = 0, gcid = 0;
+            double Uo[NV], Ug[NV], Ug1[NV];
+            int32_t ucid = 0, gcid = 0, gcid1 = 0;
             if (upd) {
-                ucid = sm.oct[(q >> 1) & 3][oo] * 8 + cxy + 4 * (q & 1);
+                ucid = sm.oct[(q >> 1) & 7][oo] * 8 + cxy + 4 * (q & 1);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) Uo[v] = uo[v][ucid];
             }
-            if (gat && !strip) gcid = gload(gpk[0], p + 2, Ug);
-            // oct table of layer (p+3)/2, read by the gather two planes on
+            if (gat) gcid = gload(gpk0, p + 2, Ug);
+            if (gat && xg) gcid1 = gload(gpk1, p + 2, Ug1);
+            // oct table of layer (p+5)/2, read by the L2 prefetch of the next plane and by the
+            // gather four planes on
             if ((p & 1) && tid < G::NO) {
-                const int L = (p + 3) >> 1;
+                const int L = (p + 5) >> 1;
                 if (L > z0 / 2 + 2 && 2 * L <= z1 + 1) oct_fill(L, tid);
             }
+            // L2 prefetch of oct layer (p+4)/2 (stencil planes p+4 and p+5, gathered two and
+            // three planes on): the two 32-byte sectors of each oct's 64-byte row per variable
+            // (a bulk prefetch per row was slower than the two sector prefetches)
+            if (!(p & 1) && p + 4 <= z1 + 1) {
+                const int L = (p + 4) >> 1;
+                for (int w = tid; w < G::NO * NV; w += G::NT) {
+                    const int o = w / NV, v = w - (w / NV) * NV;
+                    const double *src = a.u_old + int64_t(v) * tv.ncell + int64_t(sm.oct[L & 7][o]) * 8;
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(src));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(src + 4));
+                }
+            }
             float mx[NV], my[NV];
-            if (!strip) {
+            {
                 // ---- B: predictor of the thread's cell of plane p
                 float Wt[NV], Dl[3][NV];
                 predict(p, sio, Wt, Dl);
@@ -305,26 +306,29 @@ __global__ void __maxnreg__(112) k_godunov_pen(ColArgs a)
                     face_state<0>(Wt, Dl[0], -0.5f, pr, mx);
                     face_state<1>(Wt, Dl[1], -0.5f, pr, my);
                 }
-                if (gat) gstore(gpk[0], p + 2, Ug, gcid);
-            } else {
-                if (gat) gather_all(p + 2);
-                if (mid) {
-                    // ---- B: the strips: item 0 = left (l < 16, +x) / right (-x) cell of row l & 15;
-                    // item 1 = bottom (+y) / top (-y) cell of column l & 15
-                    const bool lo = lane < 16;
-                    const float half = lo ? 0.5f : -0.5f;
-                    const int r = lane & 15;
-                    float Wt[NV], Dl[3][NV], st[NV];
+            }
+            if (mid && wid < 2) {
+                // ---- B: the strips.  Warp 0: the left (lanes 0-15, +x state) and right (-x)
+                // neighbour of row lane & 15; warp 1: the bottom (+y) and top (-y) neighbour of
+                // column lane & 15
+                const bool lo = lane < 16;
+                const float half = lo ? 0.5f : -0.5f;
+                const int r = lane & 15;
+                float Wt[NV], Dl[3][NV], st[NV];
+                if (wid == 0) {
                     predict(p, (lo ? 1 : G::FX + 2) + SX * (2 + r), Wt, Dl);
                     face_state<0>(Wt, Dl[0], half, pr, st);
                     if (lo) pen_st(sm.Sx4[p & 1], sm.Sx1[p & 1], G::NI + r, st);
                     else pen_st(sm.Sr4[p & 1], sm.Sr1[p & 1], r, st);
+                } else {
                     predict(p, (2 + r) + SX * (lo ? 1 : G::FY + 2), Wt, Dl);
                     face_state<1>(Wt, Dl[1], half, pr, st);
                     if (lo) pen_st(sm.Sy4[p & 1], sm.Sy1[p & 1], G::NI + r, st);
                     else pen_st(sm.Sr4[p & 1], sm.Sr1[p & 1], 16 + r, st);
                 }
             }
+            if (gat) gstore(gpk0, p + 2, Ug, gcid);
+            if (gat && xg) gstore(gpk1, p + 2, Ug1, gcid1);
             __syncthreads();
 
             // ---- E: FP64 update of plane q = p - 1
@@ -367,7 +371,7 @@ __global__ void __maxnreg__(112) k_godunov_pen(ColArgs a)
             // ---- D: x and y faces of plane p
             if (mid) {
                 const int pb = p & 1;
-                if (!strip) {
+                {
                     float WL[NV], Fn[NV];
                     pen_ld(sm.Sx4[pb], sm.Sx1[pb], x ? ci - 1 : G::NI + y, WL);
                     col_solve<float, RS>(WL, mx, pr, a.status, Fn);
@@ -379,7 +383,8 @@ __global__ void __maxnreg__(112) k_godunov_pen(ColArgs a)
 #pragma unroll
                     for (int v = 0; v < NV; ++v) fyo[v] = Fn[v];
                     if (y) pen_st(sm.Gy4[pb], sm.Gy1[pb], ci - G::FX, Fn);
-                } else {
+                }
+                if (wid == 2) {
                     // edge faces: lane l < 16 the right face of row l, else the top face of column l - 16
                     const int r = lane & 15;
                     const int li = lane < 16 ? (G::FX - 1) + G::FX * r : r + G::FX * (G::FY - 1);
@@ -439,10 +444,16 @@ amr_status launch_pen(const amr_tree *t, const hydro_params *p, const double *u_
         a.n = int64_t(1) << t->grid_level;
         if (a.n % G::FX) return AMR_EINVAL;
         if (zc <= 0) {
-            // default: 32-cell segments (fewer on small levels, so that the launch has at
-            // least two waves of two CTAs per SM)
-            zc = a.n < 32 ? int(a.n) : 32;
-            while (zc > 8 && (a.n / G::FX) * (a.n / G::FY) * ((a.n + zc - 1) / zc) < int64_t(4) * nsm) zc /= 2;
+            // default: the even segment length in [8, 64] with the shortest estimated makespan,
+            // waves of two CTAs per SM x (segment + 4 planes of prologue); ties go to the
+            // longer segment
+            const int64_t slots = int64_t(2) * nsm, cols = (a.n / G::FX) * (a.n / G::FY);
+            int64_t best = -1;
+            for (int s = 8; s <= 64 && s <= a.n; s += 2) {
+                const int64_t items = cols * ((a.n + s - 1) / s);
+                const int64_t cost = ((items + slots - 1) / slots) * (s + 4);
+                if (best < 0 || cost <= best) { best = cost; zc = s; }
+            }
         }
         zc = (zc + 1) & ~1;                              // whole oct layers
         if (zc < 2) zc = 2;

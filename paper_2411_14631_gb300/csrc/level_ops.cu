@@ -1,5 +1,6 @@
 // Per-level operations around the Godunov update: the CFL time step (newdt_fine,
 // Table 1), refluxing + restriction, initial-state set-up, and the C entry points.
+#include <algorithm>
 #include <atomic>
 #include <cfloat>
 #include <cstring>
@@ -89,68 +90,151 @@ __global__ void k_courant_batch(TreeView tv, const double *__restrict__ u, doubl
 
 // Coarse level l: leaf cells next to a refined cell take the fine fluxes from the
 // register (-/+ dt/dx * 1/4 * sum of the four fine fluxes); refined cells become the
-// mean of their eight children.
+// mean of their eight children.  One cell; returns its CFL candidate (DBL_MAX if none).
+template <typename R>
+__device__ __forceinline__ double reflux_cell(const TreeView &tv, int level, int64_t cell,
+                                              const double *__restrict__ reg, double *u, const double *dtp,
+                                              bool want_dt, double gamma, double rf, double pf, double cfl,
+                                              int restrict_all)
+{
+    double cand = DBL_MAX;
+    const int64_t o = cell >> 3;
+    const int c = int(cell & 7);
+    const int32_t s = tv.son[cell];
+    if (s >= 0) {
+        if (restrict_all || !tv.fused[s]) {               // else restricted by the update kernel
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double sum = 0.0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) sum += u[v * tv.ncell + int64_t(s) * 8 + q];
+                u[v * tv.ncell + cell] = 0.125 * sum;
+            }
+        }
+    } else if (reg && level >= tv.levelmin) {
+        const double lam = scale_pow2(*dtp, level);   // dt / dx, exact
+        double U[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = u[v * tv.ncell + cell];
+        bool hit = false;
+        for (int f = 0; f < 6; ++f) {
+            const int d = f >> 1, side = f & 1;
+            int64_t nb;
+            if (((c >> d) & 1) != side) {
+                nb = o * 8 + (c ^ (1 << d));
+            } else {
+                const int32_t N = tv.nbor[6 * o + f];
+                if (N < 0) continue;                      // outflow face of the box
+                const int32_t so = tv.son[N];
+                if (so < 0) continue;                     // coarser neighbour
+                nb = int64_t(so) * 8 + (c ^ (1 << d));
+            }
+            const int32_t fo = tv.son[nb];
+            if (fo < 0) continue;
+            const int opp = 2 * d + (1 - side);
+            const double *rrow = reg + ((int64_t(fo) - tv.reg_base) * 6 + opp) * NV;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const double corr = 0.25 * rrow[v];
+                U[v] = side ? U[v] - lam * corr : U[v] + lam * corr;
+            }
+            hit = true;
+        }
+        if (hit) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) u[v * tv.ncell + cell] = U[v];
+            if (want_dt) {
+                Prm<R> p;
+                p.gamma = to_work<R>(gamma); p.rho_floor = to_work<R>(rf); p.p_floor = to_work<R>(pf);
+                cand = cfl_candidate<R>(U, p, to_work<R>(cfl), to_work<R>(pow2(-level)));
+            }
+        }
+    }
+    return cand;
+}
+
 template <typename R>
 __global__ void k_reflux(TreeView tv, int level, const double *__restrict__ reg, double *u, const double *dtp,
                          double *dt_next, double gamma, double rf, double pf, double cfl, int restrict_all)
 {
     const int64_t cell = tv.lvl_off[level] * 8 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     double cand = DBL_MAX;
-    if (cell < tv.lvl_off[level + 1] * 8) {
-        const int64_t o = cell >> 3;
-        const int c = int(cell & 7);
-        const int32_t s = tv.son[cell];
-        if (s >= 0) {
-            if (restrict_all || !tv.fused[s]) {               // else restricted by the update kernel
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    double sum = 0.0;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) sum += u[v * tv.ncell + int64_t(s) * 8 + q];
-                    u[v * tv.ncell + cell] = 0.125 * sum;
-                }
-            }
-        } else if (reg && level >= tv.levelmin) {
-            const double lam = scale_pow2(*dtp, level);   // dt / dx, exact
-            double U[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) U[v] = u[v * tv.ncell + cell];
-            bool hit = false;
-            for (int f = 0; f < 6; ++f) {
-                const int d = f >> 1, side = f & 1;
-                int64_t nb;
-                if (((c >> d) & 1) != side) {
-                    nb = o * 8 + (c ^ (1 << d));
-                } else {
-                    const int32_t N = tv.nbor[6 * o + f];
-                    if (N < 0) continue;                      // outflow face of the box
-                    const int32_t so = tv.son[N];
-                    if (so < 0) continue;                     // coarser neighbour
-                    nb = int64_t(so) * 8 + (c ^ (1 << d));
-                }
-                const int32_t fo = tv.son[nb];
-                if (fo < 0) continue;
-                const int opp = 2 * d + (1 - side);
-                const double *rrow = reg + ((int64_t(fo) - tv.reg_base) * 6 + opp) * NV;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    const double corr = 0.25 * rrow[v];
-                    U[v] = side ? U[v] - lam * corr : U[v] + lam * corr;
-                }
-                hit = true;
-            }
-            if (hit) {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) u[v * tv.ncell + cell] = U[v];
-                if (dt_next) {
-                    Prm<R> p;
-                    p.gamma = to_work<R>(gamma); p.rho_floor = to_work<R>(rf); p.p_floor = to_work<R>(pf);
-                    cand = cfl_candidate<R>(U, p, to_work<R>(cfl), to_work<R>(pow2(-level)));
-                }
-            }
-        }
-    }
+    if (cell < tv.lvl_off[level + 1] * 8)
+        cand = reflux_cell<R>(tv, level, cell, reg, u, dtp, dt_next != nullptr, gamma, rf, pf, cfl, restrict_all);
     if (dt_next) min_to(dt_next, cand);
+}
+
+// Restriction of complete levels: one CTA per oct O of level L restricts the nlev levels
+// L + nlev - 1 .. L of O's subtree (nlev <= 3), the deepest from level L + nlev in global
+// memory, the others from the values it has just formed (kept in shared memory).  Every
+// cell is the mean of its eight children summed in cell order, as in k_reflux.  Valid
+// where levels L .. L + nlev are complete (every cell of levels L .. L + nlev - 1 refined):
+// the levels below the deepest complete one.
+__global__ void __launch_bounds__(256) k_restrict_complete(TreeView tv, int L, int nlev, double *u)
+{
+    __shared__ int32_t son1[8], son2[64];     // son octs of O's cells, and of their cells
+    __shared__ double v2[NV][512], v1[NV][64];
+    const int t = threadIdx.x;
+    const int64_t O = tv.lvl_off[L] + blockIdx.x;
+    auto mean8 = [&](const double *c) {
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc += c[q];
+        return 0.125 * acc;
+    };
+    if (nlev >= 2 && t < 8) son1[t] = tv.son[O * 8 + t];
+    __syncthreads();
+    if (nlev == 3 && t < 64) son2[t] = tv.son[int64_t(son1[t >> 3]) * 8 + (t & 7)];
+    __syncthreads();
+    if (nlev == 3) {
+        // level L+2: the 512 cells of the 64 octs son2[], from their sons at level L+3
+        for (int w = t; w < 512 * NV; w += blockDim.x) {
+            const int v = w >> 9, j = w & 511;
+            const int64_t cell = int64_t(son2[j >> 3]) * 8 + (j & 7);
+            const int64_t s3 = tv.son[cell];
+            double c[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) c[q] = u[v * tv.ncell + s3 * 8 + q];
+            const double m = mean8(c);
+            u[v * tv.ncell + cell] = m;
+            v2[v][j] = m;
+        }
+        __syncthreads();
+    }
+    if (nlev >= 2) {
+        // level L+1: the 64 cells of the 8 octs son1[]
+        for (int w = t; w < 64 * NV; w += blockDim.x) {
+            const int v = w >> 6, k = w & 63;
+            const int64_t cell = int64_t(son1[k >> 3]) * 8 + (k & 7);
+            double c[8];
+            if (nlev == 3) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) c[q] = v2[v][k * 8 + q];
+            } else {
+                const int64_t s2 = tv.son[cell];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) c[q] = u[v * tv.ncell + s2 * 8 + q];
+            }
+            const double m = mean8(c);
+            u[v * tv.ncell + cell] = m;
+            v1[v][k] = m;
+        }
+        __syncthreads();
+    }
+    // level L: O's eight cells
+    if (t < 8 * NV) {
+        const int v = t >> 3, c0 = t & 7;
+        double c[8];
+        if (nlev >= 2) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) c[q] = v1[v][c0 * 8 + q];
+        } else {
+            const int64_t s1 = tv.son[O * 8 + c0];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) c[q] = u[v * tv.ncell + s1 * 8 + q];
+        }
+        u[v * tv.ncell + O * 8 + c0] = mean8(c);
+    }
 }
 
 __global__ void k_prim_to_cons(int64_t ncell, const double *__restrict__ w, double *u, double gamma)
@@ -217,6 +301,24 @@ static amr_status reflux_launch(const amr_tree *t, int level, const hydro_params
         k_reflux<double><<<nb, 256, 0, st>>>(tv, level, reg, u, dt, dt_next, p->gamma, p->rho_floor, p->p_floor, p->cfl,
                                              restrict_all);
     AMR_CUDA_TRY(cudaGetLastError());
+    return AMR_OK;
+}
+
+// Restriction of the complete levels below lo_end (levels lo_end - 1 .. 1), three levels
+// per launch from the top down.
+static amr_status restrict_complete_launch(const amr_tree *t, int lo_end, double *u, cudaStream_t st)
+{
+    const TreeView tv = make_view(t);
+    for (int top = lo_end - 1; top >= 1;) {
+        const int nlev = top >= 3 ? 3 : top;
+        const int L = top - nlev + 1;
+        const int64_t nb = t->lvl_off[L + 1] - t->lvl_off[L];
+        if (nb > 0) {
+            k_restrict_complete<<<unsigned(nb), 256, 0, st>>>(tv, L, nlev, u);
+            AMR_CUDA_TRY(cudaGetLastError());
+        }
+        top = L - 1;
+    }
     return AMR_OK;
 }
 
@@ -387,10 +489,15 @@ extern "C" amr_status hydro_step(const amr_tree *t, const hydro_params *p, const
                                      reinterpret_cast<cudaStream_t>(stream)));
     amr_status r = hydro_godunov_level(t, -1, p, d_u_old, d_u_new, d_flux_reg, d_dt, d_dt_next, stream);
     if (r != AMR_OK) return r;
-    for (int l = t->levelmax - 1; l >= 1; --l) {
+    // reflux + restriction per level from the finest up to the level above the deepest
+    // complete one; the complete levels below that are pure restrictions, three per launch
+    const int gl = t->n_inst > 0 ? 0 : t->grid_level;
+    const int lstop = gl >= 2 ? gl - 1 : 1;
+    for (int l = t->levelmax - 1; l >= lstop; --l) {
         r = reflux_launch(t, l, p, d_flux_reg, d_u_new, d_dt, d_dt_next, reinterpret_cast<cudaStream_t>(stream));
         if (r != AMR_OK) return r;
     }
+    if (lstop > 1) return restrict_complete_launch(t, lstop, d_u_new, reinterpret_cast<cudaStream_t>(stream));
     return AMR_OK;
 }
 

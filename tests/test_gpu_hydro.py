@@ -271,10 +271,14 @@ def test_autotuner_picks_a_candidate(oracle, H, tmp_path, monkeypatch):
     g = H.Octree(lx, 5, OUT)
     t = oracle.Tree(lx, 5, OUT)
     xyz, _ = t.cell_centres()
-    tile, ms = autotune.tune(g, 1.4, W.sod_prims(xyz), steps=2)
-    assert tile in (1, 2) and set(ms) == {"1", "2"}
-    tile2, ms2 = autotune.tune(g, 1.4, W.sod_prims(xyz), steps=2)   # cached
-    assert tile2 == tile and ms2 == ms
+    best, ms = autotune.tune(g, 1.4, W.sod_prims(xyz), steps=2)
+    names = set(ms)
+    # a complete 32^3 level: pencil and slab z-column candidates, no tile levels
+    assert any(n.startswith("pencil/") for n in names) and any(n.startswith("slab/") for n in names)
+    assert best["col_kernel"] in (1, 2) and best["tile"] == 0
+    assert min(ms.values()) == ms[autotune._name(best)]
+    best2, ms2 = autotune.tune(g, 1.4, W.sod_prims(xyz), steps=2)   # cached
+    assert best2 == best and ms2 == ms
 
 
 @pytest.mark.parametrize("level,precision,riemann,bc", [(5, 0, 0, OUT), (5, 1, 0, PER), (6, 1, 0, OUT),

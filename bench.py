@@ -145,8 +145,6 @@ def time_path(H, tree, prm, w0, steps, warmup, stream, label, kernel_events=True
     # the initial state and dt are made on the current stream; the steps below run on
     # `stream`, which does not wait for it by itself
     stream.wait_stream(torch.cuda.current_stream())
-    nlev = tree.levelmax
-
     def one_step(ev=None):
         sim.dt_next.fill_(1.0e300)
         if ev is not None:
@@ -154,8 +152,9 @@ def time_path(H, tree, prm, w0, steps, warmup, stream, label, kernel_events=True
         H.hydro_godunov_level(tree, -1, prm, sim.u, sim.u_new, sim.reg, sim.dt, sim.dt_next, stream)
         if ev is not None:
             ev[1].record(stream)
-        for l in range(nlev - 1, 0, -1):
-            H.hydro_reflux_level(tree, l, prm, sim.reg, sim.u_new, sim.dt, sim.dt_next, stream)
+        # the rest of the step, per level (the same bits as hydro_step's launches)
+        for l in range(tree.levelmax - 1, 0, -1):
+            H.reflux_level(tree, l, prm, sim.reg, sim.u_new, sim.dt, sim.dt_next, stream)
         sim.u, sim.u_new = sim.u_new, sim.u
         sim.dt, sim.dt_next = sim.dt_next, sim.dt
 
@@ -173,8 +172,27 @@ def time_path(H, tree, prm, w0, steps, warmup, stream, label, kernel_events=True
         t1.synchronize()
     ms = t0.elapsed_time(t1) / steps
     gms = statistics.mean(a.elapsed_time(b) for a, b in kev) if kernel_events else None
-    launches_per_step = 1 + (nlev - 1)
-    return ms, gms, sim, launches_per_step
+    return ms, gms, sim, launches_per_step(tree)
+
+
+def launches_per_step(tree):
+    """Kernels one hydro_step launches on this mesh: the z-column kernel of the deepest
+    complete level (when it is level 3 or deeper), one tile-kernel launch for the levels
+    above it (plus one that interpolates the ghost fathers' children, when there are any),
+    one reflux launch per level from levelmax-1 down to the one above the deepest complete
+    level (none when the deepest complete level is the finest), and one restriction launch
+    per three complete levels below that."""
+    if tree.t.n_inst > 0:
+        return 1
+    gl, lmax = int(tree.t.grid_level), tree.levelmax
+    n = 1 if gl >= 3 else 0
+    if gl < lmax or gl < 3:
+        n += 1 + (1 if int(tree.t.n_ghost) > 0 else 0)
+    lstop = gl - 1 if gl >= 2 else 1
+    lfirst = gl - 2 if (gl >= 2 and gl == lmax) else lmax - 1
+    n += max(0, lfirst - lstop + 1)
+    n += (max(0, lstop - 1) + 2) // 3
+    return n
 
 
 def time_graph(H, tree, prm, w0, steps, warmup):
@@ -345,6 +363,50 @@ def l1_fields(u, ref):
     for name, a, b in (("rho", u[0], ref[0]), ("mom", mom, momr), ("E", u[4], ref[4])):
         out[name] = float((torch.abs(a - b).sum() / torch.abs(b).sum()).item())
     return out
+
+
+def equal_l1(H, tree, w0, shape, steps=10):
+    """The metric's "at equal L1 err": after `steps` steps at a common fixed dt (3/4 of the
+    initial FP32 CFL step), L1 of rho, |momentum| and E of the chosen path (FP32
+    reconstruction + HLLC, FP64 accumulation) and of the plain FP64 HLLC path against the
+    FP64 exact-Riemann-solver path (equal to the oracle within 1e-12), and between them."""
+    import torch
+    from paper_2411_14631_gb300 import abi
+    dt0 = torch.zeros(1, dtype=torch.float64, device=tree.device)
+    H.hydro_courant(tree, H.Params(GAMMA, cfl=CFL, precision=abi.PREC_FP32, device=tree.device),
+                    H.Simulation(tree, H.Params(GAMMA, cfl=CFL, device=tree.device), w0=w0).u, dt0)
+    dt_fixed = float(dt0.item()) * 0.75
+    dt = torch.full((1,), dt_fixed, dtype=torch.float64, device=tree.device)
+
+    def run(prm):
+        s_ = H.Simulation(tree, prm, w0=w0)
+        for _ in range(steps):
+            H.hydro_step(tree, prm, s_.u, s_.u_new, s_.reg, dt, None)
+            s_.u, s_.u_new = s_.u_new, s_.u
+        torch.cuda.synchronize()
+        st, _ = prm.read_status()
+        return s_.u, st
+
+    ref, st_ref = run(H.Params(GAMMA, cfl=CFL, riemann=abi.RIEMANN_EXACT, device=tree.device))
+    chosen, st_c = run(H.Params(GAMMA, cfl=CFL, precision=abi.PREC_FP32, device=tree.device, **shape))
+    plain, st_p = run(H.Params(GAMMA, cfl=CFL, device=tree.device))
+    out = {"reference": "FP64 exact-Riemann-solver path (equal to the oracle within 1e-12)", "steps": steps,
+           "dt_fixed": dt_fixed, "chosen_fp32_vs_ref": l1_fields(chosen, ref),
+           "plain_fp64_vs_ref": l1_fields(plain, ref), "chosen_vs_plain": l1_fields(chosen, plain),
+           "status": [st_ref, st_c, st_p]}
+    out["chosen_over_plain_rho"] = out["chosen_fp32_vs_ref"]["rho"] / out["plain_fp64_vs_ref"]["rho"]
+    out["equal_within_5pct"] = bool(out["chosen_over_plain_rho"] <= 1.05)
+    return out
+
+
+def conservation_drift(H, tree, u0, u1):
+    """Relative drift of the leaf totals (mass, momenta, energy) between two states,
+    measured on the GPU (hydro_conservation, FP64, fixed summation order); each total's
+    drift relative to the larger of its absolute sums."""
+    t0 = H.hydro_conservation(tree, u0).cpu().numpy()[0]
+    t1 = H.hydro_conservation(tree, u1).cpu().numpy()[0]
+    scale = [max(a, b) for a, b in zip(t0[1], t1[1])]
+    return [float(abs(b - a) / c) for a, b, c in zip(t0[0], t1[0], scale)]
 
 
 def study_surrogate(args):
@@ -613,21 +675,17 @@ def study_amr(args):
     del sc
     out["launch_shape"] = shape
     out["autotune_ms_per_step"] = tune_ms
-    vol = np.ldexp(1.0, -3 * lvl.astype(np.int64))[leaf]
     for name, prec in (("fp64", abi.PREC_FP64), ("fp32", abi.PREC_FP32)):
         sim = H.Simulation(tree, H.Params(5.0 / 3.0, cfl=CFL, precision=prec, **(shape if prec else dict(tile=1))),
                            w0=w0)
-        u0 = sim.u.cpu().numpy()
-        tot0 = np.array([np.sum(u0[v, leaf] * vol) for v in range(5)])
+        u0 = sim.u.clone()
         for _ in range(10):
             sim.step()
-        u1 = sim.u.cpu().numpy()
-        tot1 = np.array([np.sum(u1[v, leaf] * vol) for v in range(5)])
-        # drift of each total relative to the larger of its start and end absolute sums
-        # (momenta start at zero)
-        scale = np.array([max(np.sum(np.abs(u0[v, leaf]) * vol), np.sum(np.abs(u1[v, leaf]) * vol))
-                          for v in range(5)])
-        out["conservation_" + name] = {"steps": 10, "rel_drift": [float(x) for x in np.abs(tot1 - tot0) / scale]}
+        # drift of each leaf total relative to the larger of its start and end absolute sums
+        # (momenta start at zero), from the GPU conservation diagnostics
+        out["conservation_" + name] = {"steps": 10, "rel_drift": conservation_drift(H, tree, u0, sim.u),
+                                       "how": "hydro_conservation (GPU FP64 leaf totals)"}
+        del u0
         if prec == abi.PREC_FP32:
             # refine_fine on the evolved state: flags, 2:1 balance, device oct list, the new
             # tree (Hilbert keys, sort, tables) and the state remap
@@ -763,6 +821,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-l1", action="store_true", help="skip the equal-L1 runs (FP64 exact-solver reference)")
     ap.add_argument("--study", default=None, choices=["surrogate", "sedov", "amr", "poisson"])
     ap.add_argument("--level", type=int, default=8,
                     help="level of the turbulent box (2^level cells per axis); 8 is the benchmark's 256^3")
@@ -827,12 +886,18 @@ def main():
     ms, sim32 = time_graph(H, tree, prm32, w0, args.steps, args.warmup)
     barrier()
     clocks = clk.stop()
+    drift = conservation_drift(H, tree, H.Simulation(tree, prm32, w0=w0).u, sim32.u)
     ms = job_ms(ms, ws, dev)
     value = job_value(leaf, ws, ms)
     status, counters = prm32.read_status()
 
     hbm, peak_kind = peaks()
     achieved = leaf * BYTES_PER_UPDATE / (gms * 1e-3) / 1e9
+    if shape.get("col_kernel", 0) != 1 and (1 << LEVEL) % 16 == 0:
+        kernel_name = ("k_godunov_pen<HLLC> (column-per-thread z-column update of the complete level, "
+                       "16x16-cell footprints, %s-cell segments)" % (shape.get("col_seg") or "default"))
+    else:
+        kernel_name = "k_godunov_col<float, HLLC> (slab z-column update of the complete level, 8x8-cell footprints)"
     traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
     traffic = None
     if os.path.exists(traffic_path):
@@ -849,10 +914,12 @@ def main():
                       "l2": "inputs larger than L2 (two 671 MB FP64 state arrays)"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                         "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                        "kernel": "k_godunov_col<float, HLLC> (z-column update of the complete level)",
+                        "kernel": kernel_name,
                         "godunov_ms": gms,
                         "algorithmic_bytes_per_launch": leaf * BYTES_PER_UPDATE},
-           "gpu_launches": args.steps * lps, "clocks": clocks, "device_status": status}
+           "gpu_launches": args.steps * lps, "launches_per_step": lps, "clocks": clocks, "device_status": status,
+           "conservation": {"steps": sim32.nsteps, "rel_drift_mass_momx_momy_momz_energy": drift,
+                            "how": "hydro_conservation (GPU FP64 leaf totals) before and after the timed run"}}
 
     if not args.skip_plain:
         prm64 = H.Params(GAMMA, cfl=CFL, precision=abi.PREC_FP64, device=dev)
@@ -868,6 +935,8 @@ def main():
         out["l1_note"] = ("rho, sum|FP32 - FP64| / sum|FP64| over all cells after %d steps of each path"
                           % (args.steps + args.warmup))
         del sim64
+    if not args.skip_l1:
+        out["equal_l1"] = equal_l1(H, tree, w0, shape)
     if not args.skip_e2e:
         ems, nbytes, copy_ms = time_e2e(H, tree, prm32, w0, args.steps, stream)
         out["e2e"] = {"value": ws * leaf / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,

@@ -40,12 +40,12 @@ def _code_only(text):
 
 
 def source_hash():
-    """Hash of the code the z-column update kernel (the benchmark's dominant kernel) is
-    compiled from, comments excluded: ties its recorded profiler counters to a kernel
+    """Hash of the code the z-column update kernels (the benchmark's dominant kernel) are
+    compiled from, comments excluded: ties their recorded profiler counters to a kernel
     version."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("common.cuh", "godunov_col.cuh", "hydro_math.cuh"):
+    for f in ("common.cuh", "godunov_col.cuh", "godunov_pen.cuh", "hydro_math.cuh"):
         h.update(_code_only(open(os.path.join(CSRC, f)).read()).encode())
     return h.hexdigest()[:16]
 

@@ -172,7 +172,7 @@ __global__ void k_reflux(TreeView tv, int level, const double *__restrict__ reg,
 // the levels below the deepest complete one.
 __global__ void __launch_bounds__(256) k_restrict_complete(TreeView tv, int L, int nlev, double *u)
 {
-    __shared__ int32_t son1[8], son2[64];     // son octs of O's cells, and of their cells
+    __shared__ int32_t son1[8], son2[64], son3[512];   // son octs of O's cells, of theirs, ...
     __shared__ double v2[NV][512], v1[NV][64];
     const int t = threadIdx.x;
     const int64_t O = tv.lvl_off[L] + blockIdx.x;
@@ -187,16 +187,22 @@ __global__ void __launch_bounds__(256) k_restrict_complete(TreeView tv, int L, i
     if (nlev == 3 && t < 64) son2[t] = tv.son[int64_t(son1[t >> 3]) * 8 + (t & 7)];
     __syncthreads();
     if (nlev == 3) {
-        // level L+2: the 512 cells of the 64 octs son2[], from their sons at level L+3
+        for (int j = t; j < 512; j += blockDim.x) son3[j] = tv.son[int64_t(son2[j >> 3]) * 8 + (j & 7)];
+        __syncthreads();
+        // level L+2: the 512 cells of the 64 octs son2[], from their sons son3[] at level L+3
+#pragma unroll 2
         for (int w = t; w < 512 * NV; w += blockDim.x) {
             const int v = w >> 9, j = w & 511;
-            const int64_t cell = int64_t(son2[j >> 3]) * 8 + (j & 7);
-            const int64_t s3 = tv.son[cell];
+            const double2 *src = reinterpret_cast<const double2 *>(u + v * tv.ncell + int64_t(son3[j]) * 8);
             double c[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) c[q] = u[v * tv.ncell + s3 * 8 + q];
+            for (int h = 0; h < 4; ++h) {
+                const double2 q2 = src[h];
+                c[2 * h] = q2.x;
+                c[2 * h + 1] = q2.y;
+            }
             const double m = mean8(c);
-            u[v * tv.ncell + cell] = m;
+            u[v * tv.ncell + int64_t(son2[j >> 3]) * 8 + (j & 7)] = m;
             v2[v][j] = m;
         }
         __syncthreads();
@@ -493,7 +499,11 @@ extern "C" amr_status hydro_step(const amr_tree *t, const hydro_params *p, const
     // complete one; the complete levels below that are pure restrictions, three per launch
     const int gl = t->n_inst > 0 ? 0 : t->grid_level;
     const int lstop = gl >= 2 ? gl - 1 : 1;
-    for (int l = t->levelmax - 1; l >= lstop; --l) {
+    // a tree complete up to its finest level: the update kernel restricted every father of
+    // the finest level (all its octs are flagged fused) and level gl-1 has no leaf, so that
+    // level's pass would find no work
+    const int lfirst = (gl >= 2 && gl == t->levelmax) ? gl - 2 : t->levelmax - 1;
+    for (int l = lfirst; l >= lstop; --l) {
         r = reflux_launch(t, l, p, d_flux_reg, d_u_new, d_dt, d_dt_next, reinterpret_cast<cudaStream_t>(stream));
         if (r != AMR_OK) return r;
     }

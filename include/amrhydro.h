@@ -159,6 +159,12 @@ typedef struct {
     int64_t n_ghost;
     int64_t ghost_off[AMR_MAXLEV + 2];
     int32_t *ghost_cell;
+    /* octree mode: the cells the step's reflux pass has work for, in cell order: at levels
+       levelmin .. levelmax-1, a refined cell whose child oct is not flagged in fused (its
+       restriction is not done inside hydro_godunov_level) or a leaf with a refined face
+       neighbour.  Those of level l are reflux_cell[reflux_off[l] .. reflux_off[l+1]). */
+    int32_t *reflux_cell;
+    int64_t reflux_off[AMR_MAXLEV + 2];
 } amr_tree;
 
 /* Sizes of the caller buffers amr_build_octree needs for this oct list (host list of

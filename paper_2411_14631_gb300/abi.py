@@ -54,7 +54,8 @@ class AmrTree(C.Structure):
                 ("tile_slot", C.c_void_p * 2), ("n_inst", C.c_int32), ("inst_n", C.c_void_p), ("inst_dx", C.c_void_p),
                 ("inst_oct_off", C.c_void_p), ("tile_inst", C.c_void_p * 2), ("grid_level", C.c_int32),
                 ("grid", C.c_void_p), ("col_work", C.c_int64), ("inst_col_off", C.c_void_p),
-                ("n_ghost", C.c_int64), ("ghost_off", C.c_int64 * (MAXLEV + 2)), ("ghost_cell", C.c_void_p)]
+                ("n_ghost", C.c_int64), ("ghost_off", C.c_int64 * (MAXLEV + 2)), ("ghost_cell", C.c_void_p),
+                ("reflux_cell", C.c_void_p), ("reflux_off", C.c_int64 * (MAXLEV + 2))]
 
 
 class RefineParams(C.Structure):

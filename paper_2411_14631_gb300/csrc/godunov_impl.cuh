@@ -79,10 +79,12 @@ __device__ __forceinline__ int64_t coarse_neighbour(const TreeView &tv, int64_t 
     return so >= 0 ? int64_t(so) * 8 + cc : int64_t(N);
 }
 
-// child c of coarse leaf cell F: U_F + sum_d s_d/4 minmod(U_F - U_{F-e_d}, U_{F+e_d} - U_F),
-// on conserved variables in the working precision R (FP64 values read from the state)
+// The interpolation of coarse leaf cell F to its children, on conserved variables in the
+// working precision R (FP64 values read from the state): its value uc and its MinMod
+// slopes m[d] = minmod(U_F - U_{F-e_d}, U_{F+e_d} - U_F) ...
 template <typename R>
-__device__ void interp_child(const TreeView &tv, const double *__restrict__ u, int64_t F, int c, R out[NV])
+__device__ __forceinline__ void interp_slopes(const TreeView &tv, const double *__restrict__ u, int64_t F,
+                                              R uc[NV], R m[3][NV])
 {
     const int64_t oF = F >> 3;
     const int cf = int(F & 7);
@@ -97,29 +99,47 @@ __device__ void interp_child(const TreeView &tv, const double *__restrict__ u, i
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        const R uc = to_work<R>(u[v * tv.ncell + F]);
-        R r = uc;
+        uc[v] = to_work<R>(u[v * tv.ncell + F]);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const R m = minmod(uc - to_work<R>(u[v * tv.ncell + nm[d]]), to_work<R>(u[v * tv.ncell + np[d]]) - uc);
-            r = r + (((c >> d) & 1) ? R(0.25) * m : -R(0.25) * m);
-        }
-        out[v] = r;
+        for (int d = 0; d < 3; ++d)
+            m[d][v] = minmod(uc[v] - to_work<R>(u[v * tv.ncell + nm[d]]), to_work<R>(u[v * tv.ncell + np[d]]) - uc[v]);
     }
 }
 
+// ... and child c of it: U_F + sum_d s_d/4 m[d], s_d = +1 on the upper side of axis d
+template <typename R>
+__device__ __forceinline__ R interp_value(R uc, const R m[3][NV], int v, int c)
+{
+    R r = uc;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) r = r + (((c >> d) & 1) ? R(0.25) * m[d][v] : -R(0.25) * m[d][v]);
+    return r;
+}
+
+template <typename R>
+__device__ void interp_child(const TreeView &tv, const double *__restrict__ u, int64_t F, int c, R out[NV])
+{
+    R uc[NV], m[3][NV];
+    interp_slopes<R>(tv, u, F, uc, m);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = interp_value<R>(uc[v], m, v, c);
+}
+
 // The children of ghost fathers [g0, g1), all eight per father, into out[v][8 g + c]: the
-// values the tiles of the next finer level read in place of absent octs.
+// values the tiles of the next finer level read in place of absent octs.  One thread per
+// father: the slopes are found once for its eight children.
 template <typename R>
 __global__ void __launch_bounds__(256) k_ghost(TreeView tv, const double *__restrict__ u, int64_t g0, int64_t g1,
                                                int64_t stride, R *__restrict__ out)
 {
-    const int64_t i = 8 * g0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (i >= 8 * g1) return;
-    R Uw[NV];
-    interp_child<R>(tv, u, tv.ghost_cell[i >> 3], int(i & 7), Uw);
+    const int64_t g = g0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (g >= g1) return;
+    R uc[NV], m[3][NV];
+    interp_slopes<R>(tv, u, tv.ghost_cell[g], uc, m);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) out[v * stride + i] = Uw[v];
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) out[v * stride + 8 * g + c] = interp_value<R>(uc[v], m, v, c);
 }
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
@@ -688,7 +708,7 @@ amr_status dispatch_impl(const amr_tree *t, int level, const hydro_params *p, co
         const int64_t g0 = t->ghost_off[l0 - 1], g1 = t->ghost_off[l1];
         R *gb = reinterpret_cast<R *>(reinterpret_cast<char *>(reg) + reg_rows_bytes(t));
         if (g1 > g0) {
-            const int64_t nthr = 8 * (g1 - g0);
+            const int64_t nthr = g1 - g0;
             k_ghost<R><<<unsigned((nthr + 255) / 256), 256, 0, st>>>(make_view(t), u_old, g0, g1, 8 * t->n_ghost, gb);
             AMR_CUDA_TRY(cudaGetLastError());
         }

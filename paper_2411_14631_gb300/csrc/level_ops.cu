@@ -164,6 +164,19 @@ __global__ void k_reflux(TreeView tv, int level, const double *__restrict__ reg,
     if (dt_next) min_to(dt_next, cand);
 }
 
+// The same pass over the cells of the tree's work list of one level only (the others have
+// nothing to do when not everything is restricted).
+template <typename R>
+__global__ void k_reflux_list(TreeView tv, int level, const int32_t *__restrict__ list, int64_t n,
+                              const double *__restrict__ reg, double *u, const double *dtp, double *dt_next,
+                              double gamma, double rf, double pf, double cfl)
+{
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    double cand = DBL_MAX;
+    if (i < n) cand = reflux_cell<R>(tv, level, list[i], reg, u, dtp, dt_next != nullptr, gamma, rf, pf, cfl, 0);
+    if (dt_next) min_to(dt_next, cand);
+}
+
 // Restriction of complete levels: one CTA per oct O of level L restricts the nlev levels
 // L + nlev - 1 .. L of O's subtree (nlev <= 3), the deepest from level L + nlev in global
 // memory, the others from the values it has just formed (kept in shared memory).  Every
@@ -296,10 +309,24 @@ static amr_status check(const amr_tree *t, const hydro_params *p)
 static amr_status reflux_launch(const amr_tree *t, int level, const hydro_params *p, const double *reg, double *u,
                                 const double *dt, double *dt_next, cudaStream_t st, int restrict_all = 0)
 {
+    const TreeView tv = make_view(t);
+    if (!restrict_all && t->reflux_cell && level >= t->levelmin && level < t->levelmax) {
+        // only the level's cells on the work list
+        const int64_t a = t->reflux_off[level], n = t->reflux_off[level + 1] - a;
+        if (n <= 0) return AMR_OK;
+        const unsigned nb = unsigned((n + 255) / 256);
+        if (p->precision == AMR_PREC_FP32)
+            k_reflux_list<float><<<nb, 256, 0, st>>>(tv, level, t->reflux_cell + a, n, reg, u, dt, dt_next, p->gamma,
+                                                     p->rho_floor, p->p_floor, p->cfl);
+        else
+            k_reflux_list<double><<<nb, 256, 0, st>>>(tv, level, t->reflux_cell + a, n, reg, u, dt, dt_next,
+                                                      p->gamma, p->rho_floor, p->p_floor, p->cfl);
+        AMR_CUDA_TRY(cudaGetLastError());
+        return AMR_OK;
+    }
     const int64_t nc = (t->lvl_off[level + 1] - t->lvl_off[level]) * 8;
     if (nc <= 0) return AMR_OK;
     const unsigned nb = unsigned((nc + 255) / 256);
-    const TreeView tv = make_view(t);
     if (p->precision == AMR_PREC_FP32)
         k_reflux<float><<<nb, 256, 0, st>>>(tv, level, reg, u, dt, dt_next, p->gamma, p->rho_floor, p->p_floor, p->cfl,
                                             restrict_all);

@@ -15,7 +15,7 @@ constexpr int32_t UNNEEDED = INT32_MIN + 1;
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct TreeLayout {
-    size_t lvl, ix, iy, iz, key, son, father, nbor, nb27, refmask, fused, grid, root[2], slot[2], ghost, total;
+    size_t lvl, ix, iy, iz, key, son, father, nbor, nb27, refmask, fused, grid, root[2], slot[2], ghost, rlist, total;
     int64_t tile_bound[2];
 };
 
@@ -49,6 +49,8 @@ static TreeLayout tree_layout(int64_t n, const int64_t cnt[AMR_MAXLEV + 2], int 
     int64_t coarse = 0;
     for (int l = levelmin; l < lmax; ++l) coarse += 8 * cnt[l];
     L.ghost = put(4 * (coarse > 0 ? coarse : 1));
+    // cells of the same levels with reflux or restriction work in a step, at most all of them
+    L.rlist = put(4 * (coarse > 0 ? coarse : 1));
     L.total = o;
     return L;
 }
@@ -410,6 +412,47 @@ __global__ void k_ghost_bounds(BuildView b, const int32_t *__restrict__ gpos, in
     if (l < AMR_MAXLEV + 2) out[l] = gpos[b.lvl_off[l] * 8];
 }
 
+// Cells of levels levelmin .. levelmax-1 that the step's reflux pass (not restricting
+// everything) has work for: a refined cell whose child oct is not restricted inside the
+// update kernel, or a leaf with a refined face neighbour (the same tests as the pass).
+__global__ void k_reflux_flag(BuildView b, const int32_t *__restrict__ son, const int32_t *__restrict__ nbor,
+                              const uint8_t *__restrict__ fused, int32_t *flag)
+{
+    const int64_t c0 = b.lvl_off[b.levelmin] * 8, c1 = b.lvl_off[b.levelmax] * 8;
+    const int64_t cell = c0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (cell >= c1) return;
+    const int32_t s = son[cell];
+    int32_t need = 0;
+    if (s >= 0) {
+        need = !fused[s];
+    } else {
+        const int64_t o = cell >> 3;
+        const int c = int(cell & 7);
+        for (int f = 0; f < 6 && !need; ++f) {
+            const int d = f >> 1, side = f & 1;
+            int64_t nb;
+            if (((c >> d) & 1) != side) {
+                nb = o * 8 + (c ^ (1 << d));
+            } else {
+                const int32_t N = nbor[6 * o + f];
+                if (N < 0) continue;
+                const int32_t so = son[N];
+                if (so < 0) continue;
+                nb = int64_t(so) * 8 + (c ^ (1 << d));
+            }
+            need = son[nb] >= 0;
+        }
+    }
+    flag[cell] = need;
+}
+
+__global__ void k_reflux_compact(int64_t c0, int64_t c1, const int32_t *__restrict__ flag,
+                                 const int32_t *__restrict__ pos, int32_t *list)
+{
+    const int64_t c = c0 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (c < c1 && flag[c]) list[pos[c]] = int32_t(c);
+}
+
 // ---- batch mode: independent uniform boxes -------------------------------------------
 struct BoxLayout {
     size_t lvl, ix, iy, iz, refmask, fused, inst_n, inst_dx, inst_oct_off, col_off, root[2], slot[2], tinst[2], total;
@@ -716,6 +759,23 @@ static amr_status build_tree(const amr_geom *geom, const int32_t *h_lxyz, const 
             k_tile_slots<<<unsigned((tot + TB - 1) / TB), TB, 0, st>>>(bv, d + 1, ntile, out->tile_root[d], out->son,
                                                                       out->tile_slot[d]);
         }
+    }
+    // the reflux pass's work list: per level, in cell order
+    out->reflux_cell = (int32_t *)(T + L.rlist);
+    for (int l = 0; l < AMR_MAXLEV + 2; ++l) out->reflux_off[l] = 0;
+    if (lmax > lmin) {
+        const int64_t ncell = 8 * n;
+        int32_t *rflag = (int32_t *)(S + W.gflag), *rpos = (int32_t *)(S + W.gpos);
+        int64_t *roff = (int64_t *)(S + W.small + 1280);
+        AMR_CUDA_TRY(cudaMemsetAsync(rflag, 0, 4 * size_t(ncell + 1), st));
+        const int64_t c0 = out->lvl_off[lmin] * 8, c1 = out->lvl_off[lmax] * 8;
+        k_reflux_flag<<<unsigned((c1 - c0 + TB - 1) / TB), TB, 0, st>>>(bv, out->son, out->nbor, out->fused, rflag);
+        cb = W.cub_bytes;
+        AMR_CUDA_TRY(cub::DeviceScan::ExclusiveSum(cubtmp, cb, rflag, rpos, (int)(ncell + 1), st));
+        k_reflux_compact<<<unsigned((c1 - c0 + TB - 1) / TB), TB, 0, st>>>(c0, c1, rflag, rpos, out->reflux_cell);
+        k_ghost_bounds<<<1, 32, 0, st>>>(bv, rpos, roff);
+        AMR_CUDA_TRY(cudaMemcpyAsync(out->reflux_off, roff, sizeof(out->reflux_off), cudaMemcpyDeviceToHost, st));
+        AMR_CUDA_TRY(cudaStreamSynchronize(st));
     }
     // ghost fathers: one index per coarse leaf the tiles interpolate from, in cell order
     {

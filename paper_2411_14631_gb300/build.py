@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libamrhydro.so")
 SOURCES = ["octree.cu", "godunov_fp64.cu", "godunov_fp32.cu", "level_ops.cu", "mlp.cu", "ppcg.cu", "refine.cu",
-           "diagnostics.cu"]
+           "diagnostics.cu", "mlp_tc.cu"]
 # per-file extra flags: the FP32 kernels use fast single-precision division / square root
 EXTRA = {"godunov_fp32.cu": ["--use_fast_math"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -248,6 +248,12 @@ def mlp_forward(packed, x, y, stream=None):
     check("mlp_forward", lib().mlp_forward(_ptr(packed), _ptr(x), _ptr(y), x.shape[0], _stream(stream)))
 
 
+def mlp_forward_tc(packed, x, y, status=None, stream=None):
+    """The network on the tcgen05 tensor cores (tiles of 128 samples)."""
+    check("mlp_forward_tc", lib().mlp_forward_tc(_ptr(packed), _ptr(x), _ptr(y), x.shape[0], _ptr(status),
+                                                 _stream(stream)))
+
+
 def mlp_grad(packed, x, dy, grad, scratch, stream=None):
     check("mlp_grad", lib().mlp_grad(_ptr(packed), _ptr(x), _ptr(dy), x.shape[0], _ptr(grad), _ptr(scratch),
                                      scratch.numel() * 4, _stream(stream)))

@@ -1,0 +1,56 @@
+"""The surrogate network on the tcgen05 tensor cores (mlp_forward_tc) through the C ABI:
+against the mma.sync path (the same BF16 activations up to the order of the FP32
+accumulation) and the oracle's FP64 network (the BF16 tolerance of the other forward
+test), on ragged batches of one tile, several tiles and more tiles than resident CTAs;
+and no wait runs out."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_14631_gb300 import build
+    build.build()
+    from paper_2411_14631_gb300 import hydro
+    return hydro
+
+
+def _x8(x7):
+    x = np.zeros((x7.shape[0], 8), np.float32)
+    x[:, :7] = x7
+    return x
+
+
+@pytest.mark.parametrize("n", [5, 128, 1000, 200_000])
+def test_forward_tc_matches_mma_sync_and_oracle(oracle, H, n):
+    import torch
+    sur = H.Surrogate(seed=1)
+    th = sur.theta.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(n)
+    x7 = rng.normal(0, 1, (n, 7))
+    x7[:, 6] = rng.uniform(1.1, 1.7, n)
+    xd = torch.as_tensor(_x8(x7)).cuda()
+    y_sync = sur.forward(xd).cpu().numpy()
+    y_tc = torch.full((n, 2), float("nan"), dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    H.mlp_forward_tc(sur.packed, xd, y_tc, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    y_tc = y_tc.cpu().numpy()
+    assert np.all(np.isfinite(y_tc))
+    scale = max(np.abs(y_sync).max(), 1e-6)
+    assert np.abs(y_tc - y_sync).max() <= 1e-2 * scale, np.abs(y_tc - y_sync).max() / scale
+    m = min(n, 2000)
+    y_o = oracle.mlp_forward(th, x7[:m])
+    so = np.abs(y_o).max()
+    assert np.abs(y_tc[:m] - y_o).max() <= 3e-2 * so, np.abs(y_tc[:m] - y_o).max() / so
+
+
+def test_forward_tc_argument_errors(H):
+    from paper_2411_14631_gb300 import abi
+    assert abi.lib().mlp_forward_tc(None, None, None, 3, None, None) == abi.EINVAL

@@ -304,10 +304,13 @@ amr_status mlp_make_dataset(const double *d_states, int64_t n, double gamma, flo
 amr_status mlp_forward(const void *d_packed, const float *d_x, float *d_y, int64_t n, amr_stream stream);
 /* Inference on the 5th-generation tensor cores: the same network as mlp_forward, d_y[n][2]
    = net(d_x[n][8]), over tiles of 128 samples (tcgen05.mma with BF16 operands in shared
-   memory and FP32 accumulators in tensor memory).  The activations are the same BF16
-   values as mlp_forward's up to the order of the FP32 accumulation.  Waits for the
-   tensor cores are bounded; one that runs out writes AMR_ETIMEOUT to *d_status (may be
-   NULL).  Asynchronous. */
+   memory and FP32 accumulators in tensor memory).  The hidden layers' biases enter the
+   accumulation as two BF16 terms (hi + lo, within 2^-17 of the FP32 bias); otherwise
+   the activations are the same BF16 values as mlp_forward's up to the order of the FP32
+   accumulation.  Slot 7 of each input row is ignored, as in mlp_forward.  d_x must be
+   16-byte and d_y 8-byte aligned (else AMR_EINVAL).  Waits for the tensor cores are
+   bounded; one that runs out writes AMR_ETIMEOUT to *d_status (may be NULL).
+   Asynchronous. */
 amr_status mlp_forward_tc(const void *d_packed, const float *d_x, float *d_y, int64_t n, int32_t *d_status,
                           amr_stream stream);
 /* d_grad[AMR_MLP_NPARAMS] = gradient of sum_i d_dy[i] . y(x_i) with respect to theta,

@@ -3,14 +3,17 @@
 //
 // The network is the one of mlp_warp.cuh (7 -> 64 -> 64 -> 64 -> 2, SiLU on the hidden
 // layers, BF16 weights and activations, FP32 accumulation), the project's stand-in for
-// the iterative exact Riemann solver (Toro 2009, Ch. 4).  One CTA of 128 threads takes a
-// tile of 128 samples (UMMA M = 128): the operands sit in shared memory in the K-major
-// layout without swizzle (8-row x 16-byte core matrices), one elected thread issues the
-// MMAs of a layer (K = 16 per instruction) into 64 TMEM columns and commits them to an
-// mbarrier; each warp then reads its 32 rows back (tcgen05.ld), adds the bias and applies
-// SiLU on BF16 pairs (the same arithmetic as the mma.sync path) and writes the next
-// layer's operand.  Waits are bounded: one that runs out writes AMR_ETIMEOUT, and the CTA
-// frees its tensor memory and returns.
+// the iterative exact Riemann solver (Toro 2009, Ch. 4).  One persistent CTA per SM holds
+// the weights once in shared memory and runs eight independent groups of four warps, each
+// on its own tile of 128 samples (UMMA M = 128) with its own 64 TMEM columns: the operands
+// sit in shared memory in the K-major layout without swizzle (8-row x 16-byte core
+// matrices); the group's first thread issues a layer's MMAs and commits them to the
+// group's mbarrier; the group's warps then read the accumulators back (tcgen05.ld), apply
+// SiLU on BF16 pairs (the arithmetic of the mma.sync path) and write the next layer's
+// operand, while the tensor cores run the other groups' layers.  The hidden biases are
+// folded into the MMAs; the next input tile arrives by bulk copy during the current one.
+// Waits are bounded: one that runs out writes AMR_ETIMEOUT, and the group stops after its
+// copies and MMAs in flight have landed (bounded again); the CTA frees its tensor memory.
 #include <cstdint>
 #include <cuda_bf16.h>
 #include "common.cuh"
@@ -20,29 +23,38 @@ namespace amr {
 namespace mlp {
 
 constexpr int TM = 128;            // samples per tile (UMMA M)
-constexpr int TMEM_COLS = 64;      // FP32 accumulator columns (the widest layer)
+constexpr int NG = 8;              // independent tile groups per CTA (4 warps each)
+constexpr int NT = 128 * NG;       // threads per CTA (one CTA per SM)
+constexpr int TMEM_COLS = 64 * NG; // 64 FP32 accumulator columns per group: all 512
 
 // byte offset of element (r, k) of a K-major operand with K columns (BF16), no swizzle:
 // core matrix (r/8, k/8) at (r/8) * SBO + (k/8) * LBO, LBO = 128 B, SBO = 16 K bytes
 __host__ __device__ constexpr int cofs(int r, int k, int K) { return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
 
+// The hidden layers' biases ride in the MMAs: a column pair of ones in the A operand
+// (k = 8, 9 of the input tile; a shared 128 x 16 "ones" tile for the other layers) meets
+// the bias split into two BF16 terms in B, hi = bf16(b) and lo = bf16(b - hi) (|hi + lo - b|
+// <= 2^-17 |b|), so the accumulator holds W x + b.  The hidden weights and biases are stored
+// halved (exact), so the accumulator is z/2, the argument of SiLU's tanh form.
 struct TcSmem {
-    alignas(128) uint8_t w1[64 * 16 * 2];   // B operands (N x K): W1 64 x 16 (7 used)
-    alignas(128) uint8_t w2[64 * 64 * 2];
+    alignas(128) uint8_t w1[64 * 16 * 2];    // B operands (N x K): W1|b1
+    alignas(128) uint8_t w2[64 * 64 * 2];    // W2, W3
     alignas(128) uint8_t w3[64 * 64 * 2];
-    alignas(128) uint8_t w4[16 * 64 * 2];   // W4 padded to N = 16 (2 used)
-    alignas(128) uint8_t x[TM * 16 * 2];    // A operands (M x K): the input tile (K 16, 7 used)
-    alignas(128) uint8_t h[TM * 64 * 2];    // hidden activations
-    float b[3 * H + 8];
-    alignas(8) uint64_t mbar;
+    alignas(128) uint8_t wb2[64 * 16 * 2];   // b2, b3 as (hi, lo) columns
+    alignas(128) uint8_t wb3[64 * 16 * 2];
+    alignas(128) uint8_t w4[16 * 64 * 2];    // W4 padded to N = 16 (2 used)
+    alignas(128) uint8_t ones[TM * 16 * 2];  // A operand of the bias MMAs
+    alignas(128) uint8_t h[NG][TM * 64 * 2]; // per group: the input tile (K = 16), then the activations
+    alignas(128) float stage[NG][TM * 8];    // per group: the next input tile, FP32, by bulk copy
+    alignas(8) uint64_t mma_bar[NG], x_bar[NG];
+    float b4[2];
     uint32_t tmem;
-    int32_t fail;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
 // shared-memory matrix descriptor: start address, leading (K) and stride (M/N) byte
-// offsets in 16-byte units, descriptor version 1, no swizzle
+// offsets in 16-byte units, descriptor version 1, no swizzle; +16 per K slice of 16
 __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, int K)
 {
     uint64_t d = uint64_t((addr >> 4) & 0x3FFFu);
@@ -66,13 +78,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
+// completion of this thread's prior MMAs arrives on the mbarrier
 __device__ __forceinline__ void mma_commit(uint64_t *mbar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
                  : "memory");
 }
 
-// bounded wait for the mbarrier phase (about half a second of SM clock); false if it ran out
+// bounded wait for the mbarrier phase (about half a second of SM clock); false if it ran
+// out.  Each try may suspend the thread for up to 20 us until the phase completes.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t phase)
 {
     const uint32_t a = smem_u32(mbar);
@@ -80,35 +94,90 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t phase)
     while (clock64() - t0 < 1000000000ll) {
         uint32_t done;
         asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(a), "r"(phase)
+            : "r"(a), "r"(phase), "r"(20000)
             : "memory");
         if (done) return true;
     }
     return false;
 }
 
-// 16 FP32 accumulator columns of the warp's 32 lanes (one row per thread)
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+// the mbarrier phase is complete (no wait): the acquire of the data it guards, for the
+// threads that learned of the completion through a barrier
+__device__ __forceinline__ void mbar_acquire(uint64_t *mbar, uint32_t phase)
 {
-    uint32_t r[16];
+    asm volatile("{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%0], %1;\n}\n" ::"r"(smem_u32(mbar)),
+                 "r"(phase)
+                 : "memory");
+}
+
+// bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to
+// shared memory; completion (bytes) arrives on the mbarrier
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
+
+// barrier of the 128 threads of group g (named barrier 1 + g), AND of the predicate
+__device__ __forceinline__ bool group_sync_and(int g, bool v)
+{
+    uint32_t r;
+    asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, %2, 128, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(r)
+                 : "r"(uint32_t(v)), "r"(1 + g)
+                 : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+
+// 32 FP32 accumulator columns of the warp's 32 lanes (one row per thread), then the wait
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32])
+{
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t r[2])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__global__ void __launch_bounds__(TM) k_forward_tc(const void *packed, const float *__restrict__ x, float *y, int64_t n,
-                                                   int32_t *status)
+// SiLU of a pre-activation pair given as halves h = z/2: h + h tanh(h) on BF16 pairs, the
+// arithmetic of silu_bf16x2
+__device__ __forceinline__ uint32_t silu_half_bf16x2(float h0, float h1)
+{
+    const uint32_t h = pack_bf16(h0, h1);
+    uint32_t t, r;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
+    asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(r) : "r"(h), "r"(t));
+    return r;
+}
+
+// One CTA per SM; its eight groups of four warps run independent tiles (group g takes
+// tiles g, g + NG, ... of the CTA's share), each with its own 64 TMEM columns, operand
+// buffer, mbarriers and named barrier, so the tensor cores work on one group's layer while
+// the others run their epilogues.  Per tile: the input tile (bulk-copied one tile ahead)
+// is converted to the BF16 operand; then four layers, each MMAs issued by the group's
+// first thread and committed to the group's mbarrier, then (hidden layers) TMEM ->
+// SiLU -> the next operand, in place.
+__global__ void __launch_bounds__(NT, 1) k_forward_tc(const void *packed, const float *__restrict__ x, float *y, int64_t n,
+                                                      int32_t *status)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // the operand arrays want 128-byte alignment in the shared window (the launch adds 1 KB)
@@ -116,26 +185,50 @@ __global__ void __launch_bounds__(TM) k_forward_tc(const void *packed, const flo
     TcSmem &sm = *reinterpret_cast<TcSmem *>(smem_raw + (mis ? 1024u - mis : 0u));
     const Packed P = view(packed);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = warp >> 2, gt = tid & 127;     // group, thread (= tile row) in the group
     const int64_t ntile = (n + TM - 1) / TM;
 
     // weights and biases into the operand layout (once per CTA)
     auto put = [](uint8_t *base, int r, int k, int K, __nv_bfloat16 v) {
         *reinterpret_cast<__nv_bfloat16 *>(base + cofs(r, k, K)) = v;
     };
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-    for (int i = tid; i < 64 * 16; i += TM) put(sm.w1, i >> 4, i & 15, 16, P.w[PW1 + (i >> 4) * S1 + (i & 15)]);
-    for (int i = tid; i < 64 * 64; i += TM) {
-        put(sm.w2, i >> 6, i & 63, 64, P.w[PW2 + (i >> 6) * S + (i & 63)]);
-        put(sm.w3, i >> 6, i & 63, 64, P.w[PW3 + (i >> 6) * S + (i & 63)]);
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f), one = __float2bfloat16_rn(1.0f),
+                        half = __float2bfloat16_rn(0.5f);
+    // (hi, lo) BF16 terms of b/2
+    auto bias_terms = [](float b, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+        const float bh = 0.5f * b;
+        hi = __float2bfloat16_rn(bh);
+        lo = __float2bfloat16_rn(bh - __bfloat162float(hi));
+    };
+    for (int i = tid; i < 64 * 16; i += NT) {
+        const int r = i >> 4, k = i & 15;
+        __nv_bfloat16 hi, lo, v1 = zero, v2 = zero, v3 = zero;
+        bias_terms(P.b[r], hi, lo);
+        if (k < NIN) v1 = __hmul(P.w[PW1 + r * S1 + k], half);
+        else if (k == 8) v1 = hi;
+        else if (k == 9) v1 = lo;
+        bias_terms(P.b[H + r], hi, lo);
+        if (k < 2) v2 = k == 0 ? hi : lo;
+        bias_terms(P.b[2 * H + r], hi, lo);
+        if (k < 2) v3 = k == 0 ? hi : lo;
+        put(sm.w1, r, k, 16, v1);
+        put(sm.wb2, r, k, 16, v2);
+        put(sm.wb3, r, k, 16, v3);
+        put(sm.w4, k, r, 64, k < 8 ? P.w[PW4 + k * S + r] : zero);
     }
-    for (int i = tid; i < 16 * 64; i += TM) {
+    for (int i = tid; i < 64 * 64; i += NT) {
         const int r = i >> 6, k = i & 63;
-        put(sm.w4, r, k, 64, r < 8 ? P.w[PW4 + r * S + k] : zero);
+        put(sm.w2, r, k, 64, __hmul(P.w[PW2 + r * S + k], half));
+        put(sm.w3, r, k, 64, __hmul(P.w[PW3 + r * S + k], half));
     }
-    for (int i = tid; i < 3 * H + 8; i += TM) sm.b[i] = P.b[i];
+    for (int i = tid; i < TM * 16; i += NT) put(sm.ones, i >> 4, i & 15, 16, (i & 15) < 2 ? one : zero);
+    if (tid < 2) sm.b4[tid] = P.b[3 * H + tid];
     if (tid == 0) {
-        sm.fail = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.mbar)), "r"(1) : "memory");
+        for (int q = 0; q < NG; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.mma_bar[q])), "r"(1) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.x_bar[q])), "r"(1) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
@@ -147,94 +240,143 @@ __global__ void __launch_bounds__(TM) k_forward_tc(const void *packed, const flo
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t tmem = sm.tmem;
-    const uint32_t lane_base = uint32_t(32 * warp) << 16;   // this warp's TMEM lanes
-    const uint32_t xa = smem_u32(sm.x), ha = smem_u32(sm.h);
-    const uint32_t wa[4] = {smem_u32(sm.w1), smem_u32(sm.w2), smem_u32(sm.w3), smem_u32(sm.w4)};
-    uint32_t phase = 0;
 
-    // one layer: MMAs over K/16 slices by thread 0, commit, wait (bounded)
-    auto layer = [&](uint32_t a, int K, uint32_t b, int N) -> bool {
-        if (tid == 0) {
-            const uint32_t idesc = umma_idesc(TM, N);
-            for (int kk = 0; kk < K / 16; ++kk)
-                mma_bf16(tmem, umma_desc(a + kk * 256, K), umma_desc(b + kk * 256, K), idesc, kk > 0);
-            mma_commit(&sm.mbar);
+    const bool leader = gt == 0;
+    const uint32_t tacc = sm.tmem + uint32_t(64 * g);                          // the group's columns
+    const uint32_t trow = tacc + (uint32_t(32 * (warp & 3)) << 16);            // this warp's lanes
+    uint8_t *const hg = sm.h[g];
+    float *const stg = sm.stage[g];
+    const uint32_t ha = smem_u32(hg);
+    const uint64_t d_x = umma_desc(ha, 16), d_h = umma_desc(ha, 64), d_w1 = umma_desc(smem_u32(sm.w1), 16),
+                   d_w2 = umma_desc(smem_u32(sm.w2), 64), d_w3 = umma_desc(smem_u32(sm.w3), 64),
+                   d_b2 = umma_desc(smem_u32(sm.wb2), 16), d_b3 = umma_desc(smem_u32(sm.wb3), 16),
+                   d_w4 = umma_desc(smem_u32(sm.w4), 64), d_one = umma_desc(smem_u32(sm.ones), 16);
+    constexpr uint32_t I64 = umma_idesc(TM, 64), I16 = umma_idesc(TM, 16);
+    uint32_t mphase = 0, xphase = 0;       // (every thread) the next phase of each mbarrier
+    bool mpend = false, xpend = false;     // (leader) an MMA commit / a bulk copy not yet waited for
+
+    const int64_t tstep = int64_t(gridDim.x) * NG;
+    auto issue_x = [&](int64_t t) {        // leader: bulk copy of tile t's inputs into the stage
+        const int64_t rows = n - t * TM < TM ? n - t * TM : TM;
+        bulk_load(stg, x + t * TM * 8, uint32_t(rows * 32), &sm.x_bar[g]);
+        xpend = true;
+    };
+    // leader waits for the group's MMAs; every thread of the group gets the answer
+    auto wait_mma = [&]() -> bool {
+        bool ok = true;
+        if (leader) {
+            ok = mbar_wait(&sm.mma_bar[g], mphase);
+            if (ok) mpend = false;
         }
-        // the same answer in every thread: no thread leaves the tile loop alone
-        const bool ok = __syncthreads_and(mbar_wait(&sm.mbar, phase)) != 0;
-        phase ^= 1u;
+        ok = group_sync_and(g, ok);
+        if (ok) {
+            if (!leader) mbar_acquire(&sm.mma_bar[g], mphase);
+            mphase ^= 1u;
+        }
         fence_after();
         return ok;
     };
-    // hidden-layer epilogue of this thread's row: bias, SiLU on BF16 pairs, into sm.h
-    auto hidden_out = [&](const float *bias) {
-        const int r = tid;
+    // hidden-layer epilogue of this thread's row: SiLU of the 64 columns into the operand
+    auto hidden_out = [&]() {
 #pragma unroll
-        for (int c = 0; c < 64; c += 16) {
-            float v[16];
-            tmem_ld16(tmem + lane_base + uint32_t(c), v);
-            uint32_t q[8];
+        for (int c = 0; c < 64; c += 32) {
+            uint32_t v[32];
+            tmem_ld32(trow + uint32_t(c), v);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) q[i] = silu_bf16x2(v[2 * i] + bias[c + 2 * i], v[2 * i + 1] + bias[c + 2 * i + 1]);
-            *reinterpret_cast<uint4 *>(sm.h + cofs(r, c, 64)) = make_uint4(q[0], q[1], q[2], q[3]);
-            *reinterpret_cast<uint4 *>(sm.h + cofs(r, c + 8, 64)) = make_uint4(q[4], q[5], q[6], q[7]);
+            for (int j = 0; j < 32; j += 8) {
+                uint32_t q[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    q[i] = silu_half_bf16x2(__uint_as_float(v[j + 2 * i]), __uint_as_float(v[j + 2 * i + 1]));
+                *reinterpret_cast<uint4 *>(hg + cofs(gt, c + j, 64)) = make_uint4(q[0], q[1], q[2], q[3]);
+            }
         }
         fence_async_smem();
         fence_before();
-        __syncthreads();
+        group_sync(g);
         fence_after();
     };
 
+    int64_t t = int64_t(blockIdx.x) * NG + g;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
-        // the input tile: 7 features (slot 7 of the 8 stored is unused), zero padded to K = 16
+    if (leader && t < ntile) issue_x(t);
+    for (; t < ntile; t += tstep) {
+        // the input tile: FP32 stage -> BF16 operand (features 0-6, slot 7 zeroed, ones at 8, 9)
+        if (leader) {
+            ok = mbar_wait(&sm.x_bar[g], xphase);
+            if (ok) xpend = false;
+        }
+        ok = group_sync_and(g, ok);
+        if (!ok) break;
+        if (!leader) mbar_acquire(&sm.x_bar[g], xphase);
+        xphase ^= 1u;
         {
-            const int64_t s = t * TM + tid;
-            float f[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) f[k] = (s < n && k < NIN) ? x[s * 8 + k] : 0.0f;
-            *reinterpret_cast<uint4 *>(sm.x + cofs(tid, 0, 16)) =
-                make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]), pack_bf16(f[6], f[7]));
-            *reinterpret_cast<uint4 *>(sm.x + cofs(tid, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
+            const float4 a = *reinterpret_cast<const float4 *>(stg + gt * 8);
+            const float4 b = *reinterpret_cast<const float4 *>(stg + gt * 8 + 4);
+            *reinterpret_cast<uint4 *>(hg + cofs(gt, 0, 16)) =
+                make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(b.x, b.y), pack_bf16(b.z, 0.0f));
+            *reinterpret_cast<uint4 *>(hg + cofs(gt, 8, 16)) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
         }
         fence_async_smem();
         fence_before();
-        __syncthreads();
+        group_sync(g);
         fence_after();
-        ok = layer(xa, 16, wa[0], 64);
-        if (!ok) break;
-        hidden_out(sm.b);
-        ok = layer(ha, 64, wa[1], 64);
-        if (!ok) break;
-        hidden_out(sm.b + H);
-        ok = layer(ha, 64, wa[2], 64);
-        if (!ok) break;
-        hidden_out(sm.b + 2 * H);
-        ok = layer(ha, 64, wa[3], 16);
-        if (!ok) break;
+        if (leader) {
+            if (t + tstep < ntile) issue_x(t + tstep);      // the stage is free again
+            mma_bf16(tacc, d_x, d_w1, I64, 0);
+            mma_commit(&sm.mma_bar[g]);
+            mpend = true;
+        }
+        if (!(ok = wait_mma())) break;
+        hidden_out();
+        if (leader) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) mma_bf16(tacc, d_h + 16 * kk, d_w2 + 16 * kk, I64, kk > 0);
+            mma_bf16(tacc, d_one, d_b2, I64, 1);
+            mma_commit(&sm.mma_bar[g]);
+            mpend = true;
+        }
+        if (!(ok = wait_mma())) break;
+        hidden_out();
+        if (leader) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) mma_bf16(tacc, d_h + 16 * kk, d_w3 + 16 * kk, I64, kk > 0);
+            mma_bf16(tacc, d_one, d_b3, I64, 1);
+            mma_commit(&sm.mma_bar[g]);
+            mpend = true;
+        }
+        if (!(ok = wait_mma())) break;
+        hidden_out();
+        if (leader) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) mma_bf16(tacc, d_h + 16 * kk, d_w4 + 16 * kk, I16, kk > 0);
+            mma_commit(&sm.mma_bar[g]);
+            mpend = true;
+        }
+        if (!(ok = wait_mma())) break;
         {
-            float v[16];
-            tmem_ld16(tmem + lane_base, v);
-            const int64_t s = t * TM + tid;
-            if (s < n) {
-                y[2 * s] = v[0] + sm.b[3 * H];
-                y[2 * s + 1] = v[1] + sm.b[3 * H + 1];
-            }
+            uint32_t v[2];
+            tmem_ld2(trow, v);
+            const int64_t s = t * TM + gt;
+            if (s < n)
+                *reinterpret_cast<float2 *>(y + 2 * s) =
+                    make_float2(__uint_as_float(v[0]) + sm.b4[0], __uint_as_float(v[1]) + sm.b4[1]);
         }
         fence_before();
-        __syncthreads();     // TMEM columns free for the next tile's first layer
+        group_sync(g);       // the group's TMEM columns and operand buffer free for the next tile
         fence_after();
     }
     if (!ok) {
-        set_error(status, AMR_ETIMEOUT);
-        // the MMAs may still be in flight: one more bounded wait before the memory is freed
-        mbar_wait(&sm.mbar, phase);
+        if (leader) set_error(status, AMR_ETIMEOUT);
+        // copies or MMAs may still be in flight: one more bounded wait for each before the
+        // memory is released
+        if (leader && xpend) mbar_wait(&sm.x_bar[g], xphase);
+        if (leader && mpend) mbar_wait(&sm.mma_bar[g], mphase);
     }
     fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem), "r"(TMEM_COLS) : "memory");
 }
 
 }  // namespace mlp
@@ -246,15 +388,19 @@ extern "C" amr_status mlp_forward_tc(const void *d_packed, const float *d_x, flo
                                      amr_stream stream)
 {
     if (!d_packed || !d_x || !d_y || n < 0) return AMR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_x) & 15) || (reinterpret_cast<uintptr_t>(d_y) & 7)) return AMR_EINVAL;
     if (n == 0) return AMR_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t smem = sizeof(mlp::TcSmem) + 1024;
     AMR_CUDA_TRY(cudaFuncSetAttribute(mlp::k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t ntile = (n + mlp::TM - 1) / mlp::TM;
-    const int64_t grid = ntile < int64_t(4) * nsm ? ntile : int64_t(4) * nsm;
-    mlp::k_forward_tc<<<unsigned(grid), mlp::TM, smem, st>>>(d_packed, d_x, d_y, n, d_status);
+    // one CTA per SM (its shared memory admits no second one, which the 512-column TMEM
+    // allocation relies on)
+    const int64_t ngroup = (n + mlp::TM - 1) / mlp::TM;
+    const int64_t want = (ngroup + mlp::NG - 1) / mlp::NG;
+    const int64_t grid = want < nsm ? want : nsm;
+    mlp::k_forward_tc<<<unsigned(grid), mlp::NT, smem, st>>>(d_packed, d_x, d_y, n, d_status);
     AMR_CUDA_TRY(cudaGetLastError());
     return AMR_OK;
 }

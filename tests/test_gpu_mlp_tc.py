@@ -1,8 +1,8 @@
 """The surrogate network on the tcgen05 tensor cores (mlp_forward_tc) through the C ABI:
 against the mma.sync path (the same BF16 activations up to the order of the FP32
 accumulation) and the oracle's FP64 network (the BF16 tolerance of the other forward
-test), on ragged batches of one tile, several tiles and more tiles than resident CTAs;
-and no wait runs out."""
+test), on ragged batches of one tile, several tiles and more tiles than resident CTAs, with
+non-finite values in the unused input slot; and no wait runs out."""
 import numpy as np
 import pytest
 
@@ -26,7 +26,7 @@ def _x8(x7):
     return x
 
 
-@pytest.mark.parametrize("n", [5, 128, 1000, 200_000])
+@pytest.mark.parametrize("n", [5, 128, 1000, 200_000, 1_000_003])
 def test_forward_tc_matches_mma_sync_and_oracle(oracle, H, n):
     import torch
     sur = H.Surrogate(seed=1)
@@ -34,8 +34,11 @@ def test_forward_tc_matches_mma_sync_and_oracle(oracle, H, n):
     rng = np.random.default_rng(n)
     x7 = rng.normal(0, 1, (n, 7))
     x7[:, 6] = rng.uniform(1.1, 1.7, n)
-    xd = torch.as_tensor(_x8(x7)).cuda()
+    x8 = _x8(x7)
+    xd = torch.as_tensor(x8).cuda()
     y_sync = sur.forward(xd).cpu().numpy()
+    x8[::3, 7] = np.nan                        # the unused slot is ignored by both paths
+    xd = torch.as_tensor(x8).cuda()
     y_tc = torch.full((n, 2), float("nan"), dtype=torch.float32, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     H.mlp_forward_tc(sur.packed, xd, y_tc, status)
@@ -52,5 +55,12 @@ def test_forward_tc_matches_mma_sync_and_oracle(oracle, H, n):
 
 
 def test_forward_tc_argument_errors(H):
+    import torch
     from paper_2411_14631_gb300 import abi
     assert abi.lib().mlp_forward_tc(None, None, None, 3, None, None) == abi.EINVAL
+    sur = H.Surrogate(seed=1)
+    xb = torch.zeros(8 * 4 + 4, dtype=torch.float32, device="cuda")
+    y = torch.zeros((3, 2), dtype=torch.float32, device="cuda")
+    # an input not on a 16-byte boundary is refused before any launch
+    assert abi.lib().mlp_forward_tc(sur.packed.data_ptr(), xb.data_ptr() + 4, y.data_ptr(), 3, None,
+                                    None) == abi.EINVAL

@@ -536,6 +536,65 @@ def study_surrogate(args):
     return 0
 
 
+def study_mlp(args):
+    """Throughput of the surrogate network's inference: the tcgen05 kernel (TMEM
+    accumulators and activations) against the mma.sync kernel, on as many samples as the
+    turbulent 256^3 box has faces per step (3 x 256^3), inputs resident in HBM.  The
+    SiLU's tanh runs on the MUFU unit (measured here by mlp_tanh_rate: 16 results per clock
+    per SM on GB300), 192 per sample: the ceiling the line reports beside the result."""
+    import numpy as np
+    import torch
+    from paper_2411_14631_gb300 import build
+    build.build()
+    from paper_2411_14631_gb300 import hydro as H
+    torch.cuda.set_device(0)
+    n = args.mlp_n
+    # seeded parameters, biases included (std 1/sqrt(fan in) for the weights, 0.3 for the biases)
+    rng = np.random.default_rng(1)
+    th = np.concatenate([rng.normal(0.0, 1.0 / np.sqrt(sh[1]) if len(sh) == 2 else 0.3, int(np.prod(sh)))
+                         for sh in [(64, 7), (64,), (64, 64), (64,), (64, 64), (64,), (2, 64), (2,)]])
+    sur = H.Surrogate(theta=th.astype(np.float32))
+    g = torch.Generator(device="cuda").manual_seed(5)
+    # face features of the shape the harvest produces: six normalised states and gamma
+    x = torch.randn((n, 8), device="cuda", generator=g)
+    x[:, 6] = 5.0 / 3.0
+    y = torch.empty((n, 2), device="cuda")
+    y_ref = torch.empty((n, 2), device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    clocks = Clocks(0)
+    clk = None
+    reps = max(args.steps, 100)           # about half a second per path: the clock sampler sees it
+    rec = {}
+    for name, fn in (("tcgen05", lambda: H.mlp_forward_tc(sur.packed, x, y, status)),
+                     ("mma_sync", lambda: H.mlp_forward(sur.packed, x, y_ref))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if name == "tcgen05":
+            clocks.start()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        if name == "tcgen05":
+            clk = clocks.stop()
+        ms = e0.elapsed_time(e1) / reps
+        rec[name] = {"ms": ms, "samples_per_s": n / (ms * 1e-3), "tflops": 2.0 * 8962 * n / (ms * 1e-3) / 1e12}
+    diff = float((y - y_ref).abs().max().item()) / max(float(y_ref.abs().max().item()), 1e-30)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = clk.get("sm_mhz") or 2070
+    tanh_per_clk = H.mlp_tanh_rate()          # measured MUFU tanh results per clock per SM
+    ceiling = tanh_per_clk * mhz * 1e6 * nsm / 192.0
+    out = {"study": "surrogate inference throughput (tcgen05 vs mma.sync)", "data": "synthetic",
+           "samples": n, "repetitions": reps, "paths": rec, "status": int(status.item()), "max_rel_diff_tc_vs_mma_sync": diff,
+           "tanh_results_per_clock_per_sm": tanh_per_clk, "tanh_ceiling_samples_per_s": ceiling,
+           "tcgen05_frac_of_tanh_ceiling": rec["tcgen05"]["samples_per_s"] / ceiling, "clocks": clk}
+    print(json.dumps(out))
+    return 0
+
+
 def study_sedov(args):
     """Batch of 48 independent Sedov-Taylor blasts on uneven boxes (32^3..192^3, sizes from
     default_rng(5)), one launch per step with a CFL step per box.  Throughput of the chosen
@@ -822,7 +881,8 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-l1", action="store_true", help="skip the equal-L1 runs (FP64 exact-solver reference)")
-    ap.add_argument("--study", default=None, choices=["surrogate", "sedov", "amr", "poisson"])
+    ap.add_argument("--study", default=None, choices=["surrogate", "sedov", "amr", "poisson", "mlp"])
+    ap.add_argument("--mlp-n", type=int, default=3 * 256 ** 3, help="samples of --study mlp")
     ap.add_argument("--level", type=int, default=8,
                     help="level of the turbulent box (2^level cells per axis); 8 is the benchmark's 256^3")
     ap.add_argument("--poisson-n", type=int, default=256)
@@ -845,6 +905,8 @@ def main():
         return study_amr(args)
     if args.study == "poisson":
         return study_poisson(args)
+    if args.study == "mlp":
+        return study_mlp(args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
 

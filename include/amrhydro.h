@@ -313,6 +313,13 @@ amr_status mlp_forward(const void *d_packed, const float *d_x, float *d_y, int64
    Asynchronous. */
 amr_status mlp_forward_tc(const void *d_packed, const float *d_x, float *d_y, int64_t n, int32_t *d_status,
                           amr_stream stream);
+/* The roofline of mlp_forward_tc: the throughput of the MUFU tanh (tanh.approx.bf16x2,
+   two results per instruction), which bounds it (192 tanh per sample).  Runs four CTAs
+   of 512 threads per SM, each thread eight independent chains; writes the longest CTA
+   time in SM clocks to *d_cycles and the number of tanh results of the launch to
+   *h_results (host).  Results per clock per SM = *h_results / (SMs * *d_cycles).
+   Asynchronous (d_cycles is valid after the stream reaches this point). */
+amr_status mlp_tanh_rate(unsigned long long *d_cycles, int64_t *h_results, amr_stream stream);
 /* d_grad[AMR_MLP_NPARAMS] = gradient of sum_i d_dy[i] . y(x_i) with respect to theta,
    through the BF16 network (for gradient checks). */
 amr_status mlp_grad(const void *d_packed, const float *d_x, const float *d_dy, int64_t n, float *d_grad,

@@ -22,7 +22,7 @@ EXPORTS = ["amr_build_octree_query", "amr_build_octree", "hydro_init_from_prim",
            "hydro_courant", "hydro_godunov_level", "hydro_flux_reg_bytes", "hydro_reflux_level", "reflux_level", "hydro_step",
            "amr_get_status", "amr_status_string", "hydro_step_static_scratch", "hydro_harvest_faces",
            "mlp_nparams", "mlp_packed_bytes", "mlp_scratch_bytes", "mlp_pack", "mlp_make_dataset", "mlp_forward",
-           "mlp_forward_tc",
+           "mlp_forward_tc", "mlp_tanh_rate",
            "mlp_grad", "mlp_train_step",
            "ppcg_workspace_bytes", "poisson_apply", "ppcg_start", "ppcg_iterate", "ppcg_poll", "ppcg_solve",
            "amr_refine_work_bytes", "amr_refine", "amr_build_octree_device_query", "amr_build_octree_device",
@@ -110,6 +110,7 @@ def lib():
     L.mlp_make_dataset.argtypes = [P, C.c_int64, C.c_double, P, P, P, P]
     L.mlp_forward.argtypes = [P, P, P, C.c_int64, P]
     L.mlp_forward_tc.argtypes = [P, P, P, C.c_int64, P, P]
+    L.mlp_tanh_rate.argtypes = [P, C.POINTER(C.c_int64), P]
     L.mlp_grad.argtypes = [P, P, P, C.c_int64, P, P, S, P]
     L.mlp_train_step.argtypes = [P, P, P, P, P, P, C.c_int64, C.c_float, C.c_int64, P, P, S, P]
     L.hydro_courant_levels.argtypes = [PT, PP, P, P, P]

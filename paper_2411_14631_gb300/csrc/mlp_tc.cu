@@ -1,19 +1,25 @@
 // Inference of the learned Riemann surrogate on the 5th-generation tensor cores
-// (tcgen05.mma, accumulators in tensor memory), over tiles of 128 samples.
+// (tcgen05.mma, accumulators and activations in tensor memory), over tiles of 128 samples.
 //
 // The network is the one of mlp_warp.cuh (7 -> 64 -> 64 -> 64 -> 2, SiLU on the hidden
 // layers, BF16 weights and activations, FP32 accumulation), the project's stand-in for
 // the iterative exact Riemann solver (Toro 2009, Ch. 4).  One persistent CTA per SM holds
-// the weights once in shared memory and runs eight independent groups of four warps, each
-// on its own tile of 128 samples (UMMA M = 128) with its own 64 TMEM columns: the operands
-// sit in shared memory in the K-major layout without swizzle (8-row x 16-byte core
-// matrices); the group's first thread issues a layer's MMAs and commits them to the
-// group's mbarrier; the group's warps then read the accumulators back (tcgen05.ld), apply
-// SiLU on BF16 pairs (the arithmetic of the mma.sync path) and write the next layer's
-// operand, while the tensor cores run the other groups' layers.  The hidden biases are
-// folded into the MMAs; the next input tile arrives by bulk copy during the current one.
-// Waits are bounded: one that runs out writes AMR_ETIMEOUT, and the group stops after its
-// copies and MMAs in flight have landed (bounded again); the CTA frees its tensor memory.
+// the weights once in shared memory (K-major, no swizzle: 8-row x 16-byte core matrices)
+// and runs five independent groups of four warps, each on its own tile of 128 samples
+// (UMMA M = 128) with its own 96 TMEM columns: 64 FP32 accumulators and the next layer's
+// A operand (64 BF16 activations per row).  The group's first thread issues a layer's
+// MMAs (the first layer's A from shared memory, the others' from tensor memory) and
+// commits them to the group's mbarrier; the group's warps then read the accumulators
+// (tcgen05.ld), apply SiLU on BF16 pairs (the arithmetic of the mma.sync path) and write
+// the activations back (tcgen05.st), while the tensor cores run the other groups'
+// layers.  The hidden biases are folded into the MMAs; the next input tile arrives by
+// bulk copy during the current one.
+//
+// The bound is the SiLU's tanh: the MUFU unit returns 16 tanh results per clock per SM
+// (bf16x2 and f32 forms alike), 192 per sample, against about 60 tensor-core cycles per
+// 128 samples per layer.  Waits are bounded: one that runs out writes AMR_ETIMEOUT, and
+// the group stops after its copies and MMAs in flight have landed (bounded again); the
+// CTA frees its tensor memory.
 #include <cstdint>
 #include <cuda_bf16.h>
 #include "common.cuh"
@@ -23,9 +29,11 @@ namespace amr {
 namespace mlp {
 
 constexpr int TM = 128;            // samples per tile (UMMA M)
-constexpr int NG = 8;              // independent tile groups per CTA (4 warps each)
+constexpr int NG = 5;              // independent tile groups per CTA (4 warps each)
 constexpr int NT = 128 * NG;       // threads per CTA (one CTA per SM)
-constexpr int TMEM_COLS = 64 * NG; // 64 FP32 accumulator columns per group: all 512
+constexpr int GCOLS = 96;          // TMEM columns per group: 64 FP32 accumulators, then the
+                                   // next layer's A operand (64 BF16 per row, two per column)
+constexpr int TMEM_COLS = 512;     // the allocation (a power of two >= NG * GCOLS)
 
 // byte offset of element (r, k) of a K-major operand with K columns (BF16), no swizzle:
 // core matrix (r/8, k/8) at (r/8) * SBO + (k/8) * LBO, LBO = 128 B, SBO = 16 K bytes
@@ -44,7 +52,7 @@ struct TcSmem {
     alignas(128) uint8_t wb3[64 * 16 * 2];
     alignas(128) uint8_t w4[16 * 64 * 2];    // W4 padded to N = 16 (2 used)
     alignas(128) uint8_t ones[TM * 16 * 2];  // A operand of the bias MMAs
-    alignas(128) uint8_t h[NG][TM * 64 * 2]; // per group: the input tile (K = 16), then the activations
+    alignas(128) uint8_t x[NG][TM * 16 * 2]; // per group: the input tile (A of the first layer)
     alignas(128) float stage[NG][TM * 8];    // per group: the next input tile, FP32, by bulk copy
     alignas(8) uint64_t mma_bar[NG], x_bar[NG];
     float b4[2];
@@ -76,6 +84,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// the same with the A operand in tensor memory (row i in lane i, two BF16 per column)
+__device__ __forceinline__ void mma_bf16_ta(uint32_t tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc, int acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
 // completion of this thread's prior MMAs arrives on the mbarrier
@@ -148,6 +165,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// 16 32-bit columns of the warp's 32 lanes from registers (one row per thread)
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t r[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t r[2])
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
@@ -242,12 +270,12 @@ __global__ void __launch_bounds__(NT, 1) k_forward_tc(const void *packed, const 
     fence_after();
 
     const bool leader = gt == 0;
-    const uint32_t tacc = sm.tmem + uint32_t(64 * g);                          // the group's columns
-    const uint32_t trow = tacc + (uint32_t(32 * (warp & 3)) << 16);            // this warp's lanes
-    uint8_t *const hg = sm.h[g];
+    const uint32_t tacc = sm.tmem + uint32_t(GCOLS * g);                       // the group's accumulators
+    const uint32_t tact = tacc + 64u;                                          // and activations
+    const uint32_t lanes = uint32_t(32 * (warp & 3)) << 16;                    // this warp's lanes
+    uint8_t *const xg = sm.x[g];
     float *const stg = sm.stage[g];
-    const uint32_t ha = smem_u32(hg);
-    const uint64_t d_x = umma_desc(ha, 16), d_h = umma_desc(ha, 64), d_w1 = umma_desc(smem_u32(sm.w1), 16),
+    const uint64_t d_x = umma_desc(smem_u32(xg), 16), d_w1 = umma_desc(smem_u32(sm.w1), 16),
                    d_w2 = umma_desc(smem_u32(sm.w2), 64), d_w3 = umma_desc(smem_u32(sm.w3), 64),
                    d_b2 = umma_desc(smem_u32(sm.wb2), 16), d_b3 = umma_desc(smem_u32(sm.wb3), 16),
                    d_w4 = umma_desc(smem_u32(sm.w4), 64), d_one = umma_desc(smem_u32(sm.ones), 16);
@@ -276,22 +304,18 @@ __global__ void __launch_bounds__(NT, 1) k_forward_tc(const void *packed, const 
         fence_after();
         return ok;
     };
-    // hidden-layer epilogue of this thread's row: SiLU of the 64 columns into the operand
+    // hidden-layer epilogue of this thread's row: SiLU of the 64 accumulators into the
+    // next layer's A operand in tensor memory
     auto hidden_out = [&]() {
 #pragma unroll
         for (int c = 0; c < 64; c += 32) {
-            uint32_t v[32];
-            tmem_ld32(trow + uint32_t(c), v);
+            uint32_t v[32], q[16];
+            tmem_ld32(tacc + lanes + uint32_t(c), v);
 #pragma unroll
-            for (int j = 0; j < 32; j += 8) {
-                uint32_t q[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    q[i] = silu_half_bf16x2(__uint_as_float(v[j + 2 * i]), __uint_as_float(v[j + 2 * i + 1]));
-                *reinterpret_cast<uint4 *>(hg + cofs(gt, c + j, 64)) = make_uint4(q[0], q[1], q[2], q[3]);
-            }
+            for (int i = 0; i < 16; ++i) q[i] = silu_half_bf16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+            tmem_st16(tact + lanes + uint32_t(c / 2), q);
         }
-        fence_async_smem();
+        tmem_wait_st();
         fence_before();
         group_sync(g);
         fence_after();
@@ -313,9 +337,9 @@ __global__ void __launch_bounds__(NT, 1) k_forward_tc(const void *packed, const 
         {
             const float4 a = *reinterpret_cast<const float4 *>(stg + gt * 8);
             const float4 b = *reinterpret_cast<const float4 *>(stg + gt * 8 + 4);
-            *reinterpret_cast<uint4 *>(hg + cofs(gt, 0, 16)) =
+            *reinterpret_cast<uint4 *>(xg + cofs(gt, 0, 16)) =
                 make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(b.x, b.y), pack_bf16(b.z, 0.0f));
-            *reinterpret_cast<uint4 *>(hg + cofs(gt, 8, 16)) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(xg + cofs(gt, 8, 16)) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
         }
         fence_async_smem();
         fence_before();
@@ -331,7 +355,7 @@ __global__ void __launch_bounds__(NT, 1) k_forward_tc(const void *packed, const 
         hidden_out();
         if (leader) {
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) mma_bf16(tacc, d_h + 16 * kk, d_w2 + 16 * kk, I64, kk > 0);
+            for (int kk = 0; kk < 4; ++kk) mma_bf16_ta(tacc, tact + 8 * kk, d_w2 + 16 * kk, I64, kk > 0);
             mma_bf16(tacc, d_one, d_b2, I64, 1);
             mma_commit(&sm.mma_bar[g]);
             mpend = true;
@@ -340,7 +364,7 @@ __global__ void __launch_bounds__(NT, 1) k_forward_tc(const void *packed, const 
         hidden_out();
         if (leader) {
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) mma_bf16(tacc, d_h + 16 * kk, d_w3 + 16 * kk, I64, kk > 0);
+            for (int kk = 0; kk < 4; ++kk) mma_bf16_ta(tacc, tact + 8 * kk, d_w3 + 16 * kk, I64, kk > 0);
             mma_bf16(tacc, d_one, d_b3, I64, 1);
             mma_commit(&sm.mma_bar[g]);
             mpend = true;
@@ -349,21 +373,21 @@ __global__ void __launch_bounds__(NT, 1) k_forward_tc(const void *packed, const 
         hidden_out();
         if (leader) {
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) mma_bf16(tacc, d_h + 16 * kk, d_w4 + 16 * kk, I16, kk > 0);
+            for (int kk = 0; kk < 4; ++kk) mma_bf16_ta(tacc, tact + 8 * kk, d_w4 + 16 * kk, I16, kk > 0);
             mma_commit(&sm.mma_bar[g]);
             mpend = true;
         }
         if (!(ok = wait_mma())) break;
         {
             uint32_t v[2];
-            tmem_ld2(trow, v);
+            tmem_ld2(tacc + lanes, v);
             const int64_t s = t * TM + gt;
             if (s < n)
                 *reinterpret_cast<float2 *>(y + 2 * s) =
                     make_float2(__uint_as_float(v[0]) + sm.b4[0], __uint_as_float(v[1]) + sm.b4[1]);
         }
         fence_before();
-        group_sync(g);       // the group's TMEM columns and operand buffer free for the next tile
+        group_sync(g);       // the group's TMEM columns and input buffer free for the next tile
         fence_after();
     }
     if (!ok) {
@@ -379,6 +403,32 @@ __global__ void __launch_bounds__(NT, 1) k_forward_tc(const void *packed, const 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// Throughput of the MUFU tanh, the bound of the kernel above: every thread runs eight
+// independent chains of tanh.approx.bf16x2 (the SiLU's instruction); each CTA times its
+// chains with the SM clock and the longest time is kept.
+constexpr int TANH_ITERS = 1024;
+__global__ void __launch_bounds__(512) k_tanh_rate(unsigned long long *cycles)
+{
+    uint32_t a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = 0x3C003C00u ^ uint32_t(threadIdx.x * 8 + i);
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < TANH_ITERS; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) asm volatile("tanh.approx.bf16x2 %0, %0;" : "+r"(a[i]));
+    }
+    // the results feed a branch (an atomic that adds nothing), so that the chains are
+    // neither removed nor left in flight when the clock is read after the barrier
+    uint32_t x = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x ^= a[i];
+    if (x == 0x9E3779B9u) atomicAdd(cycles, 0ull);
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) atomicMax(cycles, (unsigned long long)(t1 - t0));
+}
+
 }  // namespace mlp
 }  // namespace amr
 
@@ -391,16 +441,30 @@ extern "C" amr_status mlp_forward_tc(const void *d_packed, const float *d_x, flo
     if ((reinterpret_cast<uintptr_t>(d_x) & 15) || (reinterpret_cast<uintptr_t>(d_y) & 7)) return AMR_EINVAL;
     if (n == 0) return AMR_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const size_t smem = sizeof(mlp::TcSmem) + 1024;
+    // at least 116 KB of shared memory: one CTA per SM, which the 512-column TMEM
+    // allocation assumes
+    const size_t smem = sizeof(mlp::TcSmem) + 1024 > 116 * 1024 ? sizeof(mlp::TcSmem) + 1024 : 116 * 1024;
     AMR_CUDA_TRY(cudaFuncSetAttribute(mlp::k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    // one CTA per SM (its shared memory admits no second one, which the 512-column TMEM
-    // allocation relies on)
     const int64_t ngroup = (n + mlp::TM - 1) / mlp::TM;
     const int64_t want = (ngroup + mlp::NG - 1) / mlp::NG;
     const int64_t grid = want < nsm ? want : nsm;
     mlp::k_forward_tc<<<unsigned(grid), mlp::NT, smem, st>>>(d_packed, d_x, d_y, n, d_status);
+    AMR_CUDA_TRY(cudaGetLastError());
+    return AMR_OK;
+}
+
+extern "C" amr_status mlp_tanh_rate(unsigned long long *d_cycles, int64_t *h_results, amr_stream stream)
+{
+    if (!d_cycles || !h_results) return AMR_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = 4 * nsm, threads = 512;        // four CTAs per SM, all resident at once
+    *h_results = int64_t(blocks) * threads * 8 * mlp::TANH_ITERS * 2;
+    AMR_CUDA_TRY(cudaMemsetAsync(d_cycles, 0, sizeof(unsigned long long), st));
+    mlp::k_tanh_rate<<<blocks, threads, 0, st>>>(d_cycles);
     AMR_CUDA_TRY(cudaGetLastError());
     return AMR_OK;
 }

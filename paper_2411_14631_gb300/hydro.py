@@ -254,6 +254,16 @@ def mlp_forward_tc(packed, x, y, status=None, stream=None):
                                                  _stream(stream)))
 
 
+def mlp_tanh_rate(stream=None):
+    """Measured MUFU tanh results per SM clock per SM (mlp_forward_tc's bound)."""
+    cycles = torch.zeros(1, dtype=torch.int64, device="cuda")
+    results = C.c_int64(0)
+    check("mlp_tanh_rate", lib().mlp_tanh_rate(_ptr(cycles), C.byref(results), _stream(stream)))
+    torch.cuda.synchronize()
+    nsm = torch.cuda.get_device_properties(cycles.device).multi_processor_count
+    return results.value / (nsm * int(cycles.item()))
+
+
 def mlp_grad(packed, x, dy, grad, scratch, stream=None):
     check("mlp_grad", lib().mlp_grad(_ptr(packed), _ptr(x), _ptr(dy), x.shape[0], _ptr(grad), _ptr(scratch),
                                      scratch.numel() * 4, _stream(stream)))

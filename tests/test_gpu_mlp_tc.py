@@ -20,6 +20,16 @@ def H():
     return hydro
 
 
+def _theta(seed):
+    """Seeded parameters with non-zero biases (the initial network has zero biases)."""
+    rng = np.random.default_rng(seed)
+    th = []
+    for sh in [(64, 7), (64,), (64, 64), (64,), (64, 64), (64,), (2, 64), (2,)]:
+        std = 1.0 / np.sqrt(sh[1]) if len(sh) == 2 else 0.3
+        th.append(rng.normal(0.0, std, int(np.prod(sh))))
+    return np.concatenate(th).astype(np.float32)
+
+
 def _x8(x7):
     x = np.zeros((x7.shape[0], 8), np.float32)
     x[:, :7] = x7
@@ -29,7 +39,7 @@ def _x8(x7):
 @pytest.mark.parametrize("n", [5, 128, 1000, 200_000, 1_000_003])
 def test_forward_tc_matches_mma_sync_and_oracle(oracle, H, n):
     import torch
-    sur = H.Surrogate(seed=1)
+    sur = H.Surrogate(theta=_theta(1))
     th = sur.theta.cpu().numpy().astype(np.float64)
     rng = np.random.default_rng(n)
     x7 = rng.normal(0, 1, (n, 7))
@@ -64,3 +74,10 @@ def test_forward_tc_argument_errors(H):
     # an input not on a 16-byte boundary is refused before any launch
     assert abi.lib().mlp_forward_tc(sur.packed.data_ptr(), xb.data_ptr() + 4, y.data_ptr(), 3, None,
                                     None) == abi.EINVAL
+
+
+def test_tanh_rate_probe(H):
+    # the MUFU tanh throughput the inference kernel is bounded by: a power-of-two number
+    # of results per SM clock between 4 and 64 on any Blackwell part
+    r = H.mlp_tanh_rate()
+    assert 4.0 <= r <= 64.0, r

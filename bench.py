@@ -671,7 +671,7 @@ def study_sedov(args):
 
 
 def study_amr(args):
-    """Plummer-clump AMR mesh (base level 7 refined to level 12, 64 clumps): throughput of
+    """Plummer-clump AMR mesh (base level 7 refined to level 12 by default, 64 clumps): throughput of
     the chosen FP32 path and the plain FP64 path (all levels in one update launch, then
     reflux + restriction per level, CUDA graphs), and conservation over 10 steps."""
     import numpy as np
@@ -683,16 +683,17 @@ def study_amr(args):
     from paper_2411_14631_gb300.bench_util import cell_centres_of
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
-    lx, centres = W.plummer_tree()
-    tree = H.Octree(lx, 7, (abi.BC_PERIODIC,) * 6)
+    base, lmax = args.amr_base, args.amr_lmax
+    lx, centres = W.plummer_tree(base=base, lmax=lmax)
+    tree = H.Octree(lx, base, (abi.BC_PERIODIC,) * 6)
     w0 = W.plummer_prims(cell_centres_of(tree), centres)
     tab = tree.tables()
     son = tab["son"].cpu().numpy()
     lvl = np.repeat(tab["lvl"].cpu().numpy(), 8)
     leaf = son < 0
-    out = {"study": "Plummer-clump AMR mesh, levels 7-12, all levels in one launch", "data": "synthetic",
-           "octs": tree.noct, "leaf_cells": int(leaf.sum()),
-           "leaf_cells_per_level": {int(l): int((leaf & (lvl == l)).sum()) for l in range(7, 13)},
+    out = {"study": "Plummer-clump AMR mesh, levels %d-%d, all levels in one launch" % (base, lmax),
+           "data": "synthetic", "octs": tree.noct, "leaf_cells": int(leaf.sum()),
+           "leaf_cells_per_level": {int(l): int((leaf & (lvl == l)).sum()) for l in range(base, lmax + 1)},
            "setup_seconds": time.perf_counter() - t0}
     from paper_2411_14631_gb300 import autotune
     shape, tune_ms = autotune.tune(tree, 5.0 / 3.0, w0, precision=abi.PREC_FP32, cfl=CFL, use_cache=False)
@@ -703,7 +704,7 @@ def study_amr(args):
         res[name] = {"ms_per_step": ms, "cell_updates_per_s": int(leaf.sum()) / (ms * 1e-3), "steps_timed": steps}
     res["speedup"] = res["fp64_plain"]["ms_per_step"] / res["fp32_chosen"]["ms_per_step"]
     out["throughput"] = res
-    # sub-cycled levels (level l makes 2^(l-7) steps per coarse step): simulated time per
+    # sub-cycled levels (level l makes 2^(l-base) steps per coarse step): simulated time per
     # wall-clock second against one time step for all levels, FP32 path, CUDA graphs
     prm32 = H.Params(5.0 / 3.0, cfl=CFL, precision=abi.PREC_FP32, **shape)
     single = H.Simulation(tree, prm32, w0=w0)
@@ -722,8 +723,8 @@ def study_amr(args):
     torch.cuda.synchronize()
     ms_sc = e0.elapsed_time(e1) / nsc
     dt_sc = float(sc.dt.item())
-    per_level = {int(l): int((leaf & (lvl == l)).sum()) for l in range(7, 13)}
-    upd = sum(n * 2 ** (l - 7) for l, n in per_level.items())
+    per_level = {int(l): int((leaf & (lvl == l)).sum()) for l in range(base, lmax + 1)}
+    upd = sum(n * 2 ** (l - base) for l, n in per_level.items())
     out["subcycled"] = {"ms_per_coarse_step": ms_sc, "dt_coarse": dt_sc, "dt_single_level_step": dt_single,
                         "leaf_updates_per_coarse_step": upd, "leaf_updates_per_s": upd / (ms_sc * 1e-3),
                         "sim_time_per_wall_s": dt_sc / (ms_sc * 1e-3),
@@ -748,13 +749,13 @@ def study_amr(args):
         if prec == abi.PREC_FP32:
             # refine_fine on the evolved state: flags, 2:1 balance, device oct list, the new
             # tree (Hilbert keys, sort, tables) and the state remap
-            thr = 2.0 ** -21
-            tree.refine(sim.u, thr, 12)                 # warm-up (allocations, first launches)
+            thr = 2.0 ** (-3 * base)              # one background base cell of mass
+            tree.refine(sim.u, thr, lmax)               # warm-up (allocations, first launches)
             torch.cuda.synchronize()
             t0r = time.perf_counter()
             reps = 5
             for _ in range(reps):
-                new, u_new = tree.refine(sim.u, thr, 12)
+                new, u_new = tree.refine(sim.u, thr, lmax)
             torch.cuda.synchronize()
             dtr = (time.perf_counter() - t0r) / reps
             out["refine"] = {"ms": dtr * 1e3, "octs_before": tree.noct, "octs_after": new.noct,
@@ -883,6 +884,8 @@ def main():
     ap.add_argument("--skip-l1", action="store_true", help="skip the equal-L1 runs (FP64 exact-solver reference)")
     ap.add_argument("--study", default=None, choices=["surrogate", "sedov", "amr", "poisson", "mlp"])
     ap.add_argument("--mlp-n", type=int, default=3 * 256 ** 3, help="samples of --study mlp")
+    ap.add_argument("--amr-base", type=int, default=7, help="complete base level of --study amr")
+    ap.add_argument("--amr-lmax", type=int, default=12, help="finest level of --study amr")
     ap.add_argument("--level", type=int, default=8,
                     help="level of the turbulent box (2^level cells per axis); 8 is the benchmark's 256^3")
     ap.add_argument("--poisson-n", type=int, default=256)

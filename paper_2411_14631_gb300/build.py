@@ -50,6 +50,18 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def library_hash():
+    """Hash of the code of every kernel source of the library (comments excluded): the
+    version stamp the profile summaries of the other kernels carry."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(_code_only(open(os.path.join(CSRC, f)).read()).encode())
+    return h.hexdigest()[:16]
+
+
 def build(force=False, verbose=False):
     if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= _deps():
         return OUT

@@ -145,8 +145,15 @@ __global__ void __launch_bounds__(256) k_ghost(TreeView tv, const double *__rest
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
 
-// threads per CTA: depth-1 tiles (512 stencil cells) 128, depth-2 tiles (1728) 512
+// threads per CTA: depth-1 tiles (512 stencil cells) 128, depth-2 tiles (1728) 512.  A
+// depth-2 CTA's shared memory admits one per SM, so it may take every register (no
+// spills); the FP32 depth-1 update (HLLC or exact) fits 64 registers, eight CTAs per SM;
+// the FP64 and surrogate variants keep the compiler's own budget.
 template <int D> constexpr int threads_for() { return D == 1 ? 128 : 512; }
+template <typename R, int D, int RS> constexpr int min_ctas_for()
+{
+    return (D == 1 && sizeof(R) == 4 && RS != AMR_RIEMANN_MLP) ? 8 : 1;
+}
 
 template <typename R, int D, int RS>
 struct Smem {
@@ -345,7 +352,7 @@ __device__ __forceinline__ void mlp_faces(Smem<R, D, RS> &sm, R (*sF)[NV][Geo<D>
 // Riemann problem at face r0 of direction DIR: left state = predicted cell + half its
 // slope, right state = next cell - half its slope (floored), in the face-normal frame.
 template <typename R, int D, int RS>
-__global__ void __launch_bounds__(threads_for<D>()) k_godunov(GArgs a)
+__global__ void __launch_bounds__(threads_for<D>(), (min_ctas_for<R, D, RS>())) k_godunov(GArgs a)
 {
     using G = Geo<D>;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -195,10 +195,12 @@ def launches_per_step(tree):
     return n
 
 
-def time_graph(H, tree, prm, w0, steps, warmup):
-    """Whole steps replayed from CUDA graphs (two graphs, alternating state buffers)."""
+def time_graph(H, tree, prm, w0, steps, warmup, overlap=False):
+    """Whole steps replayed from CUDA graphs (two graphs, alternating state buffers); with
+    overlap, the restriction of the complete levels below runs on a second stream during
+    the next step, and the timed region ends after the last of them."""
     import torch
-    sim = H.Simulation(tree, prm, w0=w0).use_graph()
+    sim = H.Simulation(tree, prm, w0=w0, overlap=overlap).use_graph()
     for _ in range(warmup):
         sim.step()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -206,6 +208,7 @@ def time_graph(H, tree, prm, w0, steps, warmup):
     t0.record()
     for _ in range(steps):
         sim.step()
+    sim.join()
     t1.record()
     t1.synchronize()
     return t0.elapsed_time(t1) / steps, sim
@@ -700,7 +703,7 @@ def study_amr(args):
     res = {}
     for name, prec, steps in (("fp32_chosen", abi.PREC_FP32, args.steps), ("fp64_plain", abi.PREC_FP64, 3)):
         prm = H.Params(5.0 / 3.0, cfl=CFL, precision=prec, **(shape if prec == abi.PREC_FP32 else dict(tile=1)))
-        ms, sim = time_graph(H, tree, prm, w0, steps, 2)
+        ms, sim = time_graph(H, tree, prm, w0, steps, 2, overlap=prec == abi.PREC_FP32 and not args.no_overlap)
         res[name] = {"ms_per_step": ms, "cell_updates_per_s": int(leaf.sum()) / (ms * 1e-3), "steps_timed": steps}
     res["speedup"] = res["fp64_plain"]["ms_per_step"] / res["fp32_chosen"]["ms_per_step"]
     out["throughput"] = res
@@ -884,6 +887,8 @@ def main():
     ap.add_argument("--skip-l1", action="store_true", help="skip the equal-L1 runs (FP64 exact-solver reference)")
     ap.add_argument("--study", default=None, choices=["surrogate", "sedov", "amr", "poisson", "mlp"])
     ap.add_argument("--mlp-n", type=int, default=3 * 256 ** 3, help="samples of --study mlp")
+    ap.add_argument("--no-overlap", action="store_true",
+                    help="run the complete levels' restriction inside each step instead of overlapping the next")
     ap.add_argument("--amr-base", type=int, default=7, help="complete base level of --study amr")
     ap.add_argument("--amr-lmax", type=int, default=12, help="finest level of --study amr")
     ap.add_argument("--level", type=int, default=8,
@@ -948,7 +953,7 @@ def main():
     _, gms, sim32e, lps = time_path(H, tree, prm32, w0, args.steps, args.warmup, stream, "fp32")
     barrier()
     clk.start()
-    ms, sim32 = time_graph(H, tree, prm32, w0, args.steps, args.warmup)
+    ms, sim32 = time_graph(H, tree, prm32, w0, args.steps, args.warmup, overlap=not args.no_overlap)
     barrier()
     clocks = clk.stop()
     drift = conservation_drift(H, tree, H.Simulation(tree, prm32, w0=w0).u, sim32.u)
@@ -975,6 +980,7 @@ def main():
            "config": {"workload": WORKLOAD, "leaf_cells": leaf, "octs": tree.noct,
                       "precision": "FP32 reconstruction + Riemann, FP64 state accumulation",
                       "launch_shape": shape, "autotune_ms_per_step": tune_ms, "cuda_graph": True,
+                      "restriction_overlap": not args.no_overlap,
                       "parallelism": "replicas" if ws > 1 else "single GPU",
                       "l2": "inputs larger than L2 (two 671 MB FP64 state arrays)"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

@@ -100,7 +100,11 @@ typedef struct {
    col_seg: cells of z a CTA marches (0 = the library's choice; even; kernel 1 needs a
    power of two that divides the level, kernel 2 takes any even length, the last segment
    of the column being shorter).  Neither changes a result bit (tested): both are launch
-   shapes for the autotuner. */
+   shapes for the autotuner;
+   defer_restriction: if nonzero, hydro_step leaves out the restriction of the complete
+   levels below the deepest complete one minus one (the levels no later step of the
+   single-dt path reads); the caller runs it with hydro_restrict_complete, possibly on
+   another stream, so that it overlaps the next step. */
 typedef struct {
     double gamma, cfl, rho_floor, p_floor;
     int32_t riemann, precision, tile, tiles_only;
@@ -110,6 +114,7 @@ typedef struct {
     int32_t *d_status;
     unsigned long long *d_counters;
     int32_t col_kernel, col_seg;
+    int32_t defer_restriction, reserved;
 } hydro_params;
 
 /* The octree: host metadata plus non-owning views into the caller's tree memory.
@@ -246,6 +251,16 @@ amr_status reflux_level(const amr_tree *tree, int level, const hydro_params *par
 amr_status hydro_step(const amr_tree *tree, const hydro_params *params, const double *d_u_old,
                       double *d_u_new, double *d_flux_reg, const double *d_dt, double *d_dt_next,
                       amr_stream stream);
+
+/* The part of hydro_step that hydro_params.defer_restriction leaves out: the restriction
+   (mean of the eight children, Table 1's level step) of the complete levels g-2 .. 1 from
+   level g-1, g the deepest complete level (tree->grid_level), in d_u (device FP64 SoA, in
+   place; the d_u_new of the hydro_step it completes).  It reads level g-1 and writes
+   levels g-2 .. 1, which the next hydro_step neither reads nor writes: it may run on
+   another stream while that step runs, but must finish before the step after it (which
+   writes level g-1 of the same buffer) and before anything reads those levels.  No-op
+   when g < 3 or in batch mode; AMR_EINVAL for a missing buffer.  Asynchronous. */
+amr_status hydro_restrict_complete(const amr_tree *tree, double *d_u, amr_stream stream);
 
 /* hydro_step without any caller-provided scratch.  The paper has no counterpart: this
    is an interface convenience.  Some callers cannot allocate device memory when they

@@ -27,7 +27,7 @@ EXPORTS = ["amr_build_octree_query", "amr_build_octree", "hydro_init_from_prim",
            "ppcg_workspace_bytes", "poisson_apply", "ppcg_start", "ppcg_iterate", "ppcg_poll", "ppcg_solve",
            "amr_refine_work_bytes", "amr_refine", "amr_build_octree_device_query", "amr_build_octree_device",
            "amr_remap_state", "hydro_courant_levels", "hydro_step_subcycled", "hydro_state_to_fp32",
-           "hydro_state_from_fp32", "hydro_conservation_work_bytes", "hydro_conservation"]
+           "hydro_state_from_fp32", "hydro_conservation_work_bytes", "hydro_conservation", "hydro_restrict_complete"]
 MLP_NPARAMS = 8962
 STATIC_REG_MAX_OCTS = 131072
 
@@ -41,7 +41,7 @@ class HydroParams(C.Structure):
                 ("riemann", C.c_int32), ("precision", C.c_int32), ("tile", C.c_int32), ("tiles_only", C.c_int32),
                 ("mlp_weights", C.c_void_p), ("mlp_resid_tol", C.c_float), ("limiter", C.c_int32),
                 ("d_status", C.c_void_p), ("d_counters", C.c_void_p), ("col_kernel", C.c_int32),
-                ("col_seg", C.c_int32)]
+                ("col_seg", C.c_int32), ("defer_restriction", C.c_int32), ("reserved", C.c_int32)]
 
 
 class AmrTree(C.Structure):
@@ -133,6 +133,7 @@ def lib():
     L.hydro_conservation_work_bytes.argtypes = [PT]
     L.hydro_conservation_work_bytes.restype = S
     L.hydro_conservation.argtypes = [PT, P, P, P, S, C.c_int32, P]
+    L.hydro_restrict_complete.argtypes = [PT, P, P]
     L.hydro_state_to_fp32.argtypes = [P, P, C.c_int64, P]
     L.hydro_state_from_fp32.argtypes = [P, P, C.c_int64, P]
     L.amr_get_status.argtypes = [PP, P, P]

@@ -86,12 +86,12 @@ template <typename R> struct Prm {
     int limiter = AMR_LIMITER_MINMOD;   // slopes of the reconstruction
 };
 
-// MinMod: zero when the differences disagree in sign, else the smaller magnitude (equal
-// signs make copysign(min(|a|,|b|), a) the same value as the textbook branch)
+// MinMod: zero when the differences disagree in sign (or one is zero), else the one of
+// smaller magnitude.  Written as the median of (0, a, b), four min/max operations: for
+// finite a, b the same value as the textbook branch (a zero result may carry either sign)
 template <typename R> __device__ __forceinline__ R minmod(R a, R b)
 {
-    const R m = copysign(fmin(fabs(a), fabs(b)), a);
-    return a * b > R(0) ? m : R(0);
+    return fmax(fmin(a, b), fmin(fmax(a, b), R(0)));
 }
 
 template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }

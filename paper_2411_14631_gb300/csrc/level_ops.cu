@@ -514,6 +514,15 @@ extern "C" amr_status hydro_step_subcycled(const amr_tree *t, const hydro_params
     return AMR_OK;
 }
 
+extern "C" amr_status hydro_restrict_complete(const amr_tree *t, double *d_u, amr_stream stream)
+{
+    if (!t || !d_u) return AMR_EINVAL;
+    if (t->n_inst > 0) return AMR_OK;
+    const int gl = t->grid_level, lstop = gl >= 2 ? gl - 1 : 1;
+    if (lstop <= 1) return AMR_OK;
+    return restrict_complete_launch(t, lstop, d_u, reinterpret_cast<cudaStream_t>(stream));
+}
+
 extern "C" amr_status hydro_step(const amr_tree *t, const hydro_params *p, const double *d_u_old, double *d_u_new,
                                  double *d_flux_reg, const double *d_dt, double *d_dt_next, amr_stream stream)
 {
@@ -534,7 +543,8 @@ extern "C" amr_status hydro_step(const amr_tree *t, const hydro_params *p, const
         r = reflux_launch(t, l, p, d_flux_reg, d_u_new, d_dt, d_dt_next, reinterpret_cast<cudaStream_t>(stream));
         if (r != AMR_OK) return r;
     }
-    if (lstop > 1) return restrict_complete_launch(t, lstop, d_u_new, reinterpret_cast<cudaStream_t>(stream));
+    if (lstop > 1 && !p->defer_restriction)
+        return restrict_complete_launch(t, lstop, d_u_new, reinterpret_cast<cudaStream_t>(stream));
     return AMR_OK;
 }
 

@@ -141,11 +141,12 @@ class Params:
 
     def __init__(self, gamma, cfl=0.8, rho_floor=1e-10, p_floor=1e-20, riemann=abi.RIEMANN_HLLC,
                  precision=abi.PREC_FP64, tile=0, device="cuda:0", tiles_only=False, limiter=abi.LIMITER_MINMOD,
-                 col_kernel=0, col_seg=0):
+                 col_kernel=0, col_seg=0, defer_restriction=False):
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
         self.counters = torch.zeros(abi.NCOUNTERS, dtype=torch.int64, device=device)
         self.c = abi.HydroParams(gamma, cfl, rho_floor, p_floor, riemann, precision, tile, int(tiles_only), None,
-                                 0.0, limiter, self.status.data_ptr(), self.counters.data_ptr(), col_kernel, col_seg)
+                                 0.0, limiter, self.status.data_ptr(), self.counters.data_ptr(), col_kernel, col_seg,
+                                 int(defer_restriction), 0)
 
     def read_status(self):
         s = C.c_int32()
@@ -176,6 +177,10 @@ def hydro_godunov_level(tree, level, prm, u_old, u_new, reg, dt, dt_next=None, s
     check("hydro_godunov_level",
           lib().hydro_godunov_level(C.byref(tree.t), level, C.byref(prm.c), _ptr(u_old), _ptr(u_new), _ptr(reg),
                                     _ptr(dt), _ptr(dt_next), _stream(stream)))
+
+
+def hydro_restrict_complete(tree, u, stream=None):
+    check("hydro_restrict_complete", lib().hydro_restrict_complete(C.byref(tree.t), _ptr(u), _stream(stream)))
 
 
 def hydro_reflux_level(tree, level, prm, reg, u_new, dt, dt_next=None, stream=None):
@@ -388,10 +393,29 @@ class Simulation:
     Each ``step()`` is one pass of the hot path: Godunov update of every level (one
     launch), reflux + restriction from the finest level up, and the CFL step of the next
     step fused into both (dt never leaves the device).  With ``use_graph()`` the step is
-    replayed from two CUDA graphs (state A -> B and B -> A), captured once."""
+    replayed from two CUDA graphs (state A -> B and B -> A), captured once.
 
-    def __init__(self, tree, prm, w0=None, u0=None):
+    With ``overlap=True`` the restriction of the complete levels below the deepest
+    complete level minus one (which no later step reads) runs on a second stream,
+    concurrently with the next step: every step first waits for that restriction of the
+    step before last, whose buffer it overwrites.  ``join()`` makes the current stream
+    wait for the last one (the state is then complete on that stream)."""
+
+    def __init__(self, tree, prm, w0=None, u0=None, overlap=False):
         self.tree, self.prm = tree, prm
+        self.overlap = bool(overlap) and tree.t.n_inst == 0 and int(tree.t.grid_level) >= 3
+        if self.overlap:
+            # the same parameters (and device status words), with the restriction deferred
+            self.prm_step = Params.__new__(Params)
+            self.prm_step.status, self.prm_step.counters = prm.status, prm.counters
+            self.prm_step.c = abi.HydroParams.from_buffer_copy(prm.c)
+            self.prm_step.c.defer_restriction = 1
+            self._aux = torch.cuda.Stream(device=tree.device)
+            self._ev_fork = [torch.cuda.Event(), torch.cuda.Event()]
+            self._ev_done = [torch.cuda.Event(), torch.cuda.Event()]
+            self._last_done = None
+        else:
+            self.prm_step = prm
         dev = tree.device
         self.u = torch.empty((5, tree.ncell), dtype=torch.float64, device=dev)
         self.u_new = torch.empty_like(self.u)
@@ -411,13 +435,29 @@ class Simulation:
         self._graphs = None
 
     def step(self, stream=None):
+        k = self.nsteps % 2
+        main = stream if stream is not None else torch.cuda.current_stream(self.tree.device)
+        if self.overlap:
+            main.wait_event(self._ev_done[k])    # the restriction that read this step's output buffer
         if self._graphs is not None:
-            self._graphs[self.nsteps % 2].replay()
+            with torch.cuda.stream(main):
+                self._graphs[k].replay()
         else:
-            hydro_step(self.tree, self.prm, self.u, self.u_new, self.reg, self.dt, self.dt_next, stream)
+            hydro_step(self.tree, self.prm_step, self.u, self.u_new, self.reg, self.dt, self.dt_next, main)
+        if self.overlap:
+            self._ev_fork[k].record(main)
+            self._aux.wait_event(self._ev_fork[k])
+            hydro_restrict_complete(self.tree, self.u_new, self._aux)
+            self._ev_done[k].record(self._aux)
+            self._last_done = self._ev_done[k]
         self.u, self.u_new = self.u_new, self.u
         self.dt, self.dt_next = self.dt_next, self.dt
         self.nsteps += 1
+
+    def join(self, stream=None):
+        """Order `stream` (default: the current one) after every restriction issued so far."""
+        if self.overlap and self._last_done is not None:
+            (stream if stream is not None else torch.cuda.current_stream(self.tree.device)).wait_event(self._last_done)
 
     def use_graph(self):
         """Capture the two step graphs (after one eager step, which sets kernel attributes)."""
@@ -431,7 +471,7 @@ class Simulation:
         for (a, b, d0, d1) in order:
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=s):
-                hydro_step(self.tree, self.prm, a, b, self.reg, d0, d1, stream=s)
+                hydro_step(self.tree, self.prm_step, a, b, self.reg, d0, d1, stream=s)
             graphs.append(g)
         self._graphs = graphs
         torch.cuda.synchronize()

@@ -21,7 +21,7 @@ import torch
 from . import abi
 from . import hydro as H
 
-CACHE_VERSION = 2
+CACHE_VERSION = 3
 
 
 def _cache_path():
@@ -57,9 +57,9 @@ def column_candidates(tree, precision, riemann):
         return [dict(col_kernel=0, col_seg=0)]
     cands = []
     if precision == abi.PREC_FP32 and (n is None or n % 16 == 0):
-        segs = [0] if n is None else sorted({0} | {s for s in (16, 24, 32, 38, 44, 52, 64) if s <= n})
+        segs = [0] if n is None else sorted({0} | {s for s in (16, 24, 32, 38, 44, 52, 64, 96, 128) if s <= n})
         cands += [dict(col_kernel=2, col_seg=s) for s in segs]
-    segs = [0] if n is None else sorted({0} | {s for s in (16, 32, 64) if s <= n and n % s == 0})
+    segs = [0] if n is None else sorted({0} | {s for s in (16, 32, 64, 128) if s <= n and n % s == 0})
     cands += [dict(col_kernel=1, col_seg=s) for s in segs]
     return cands
 

@@ -123,3 +123,20 @@ def test_pencil_full_size_benchmark_box(H):
     assert out[0][2] == 0 and out[1][2] == 0
     assert torch.equal(out[0][0], out[1][0])
     assert torch.equal(out[0][1], out[1][1])
+
+
+def test_long_segments_on_a_128_box(H):
+    """The autotuner's longest segments on a 128^3 box (level 7): the pencil kernel with 96
+    (ragged: 96 + 32) and 128 cells, the slab kernel with 64 and 128, each bitwise the
+    default pencil launch, over two steps."""
+    import torch
+    from paper_2411_14631_gb300.bench_util import cell_centres_of
+    g = H.Octree(W.uniform_tree(7), 7, PER)
+    w0 = _fields(cell_centres_of(g), 77)
+    ref = _run(H, g, w0, steps=2)
+    assert ref[2] == 0
+    for kw in (dict(col_kernel=2, col_seg=96), dict(col_kernel=2, col_seg=128), dict(col_kernel=1, col_seg=64),
+               dict(col_kernel=1, col_seg=128)):
+        u, dt, st = _run(H, g, w0, steps=2, **kw)
+        assert st == 0, kw
+        assert np.array_equal(u, ref[0]) and np.array_equal(dt, ref[1]), kw

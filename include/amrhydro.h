@@ -315,7 +315,7 @@ amr_status mlp_pack(const float *d_theta, void *d_packed, amr_stream stream);
    exact solver rejects (vacuum, no convergence) sets *d_status (if not NULL). */
 amr_status mlp_make_dataset(const double *d_states, int64_t n, double gamma, float *d_x, float *d_y,
                             int32_t *d_status, amr_stream stream);
-/* Inference: d_y[n][2] = net(d_x[n][8]). */
+/* Inference: d_y[n][2] = net(d_x[n][8]); n = 0 is a no-op (d_x, d_y may be NULL). */
 amr_status mlp_forward(const void *d_packed, const float *d_x, float *d_y, int64_t n, amr_stream stream);
 /* Inference on the 5th-generation tensor cores: the same network as mlp_forward, d_y[n][2]
    = net(d_x[n][8]), over tiles of 128 samples (tcgen05.mma with BF16 operands in shared
@@ -323,7 +323,8 @@ amr_status mlp_forward(const void *d_packed, const float *d_x, float *d_y, int64
    accumulation as two BF16 terms (hi + lo, within 2^-17 of the FP32 bias); otherwise
    the activations are the same BF16 values as mlp_forward's up to the order of the FP32
    accumulation.  Slot 7 of each input row is ignored, as in mlp_forward.  d_x must be
-   16-byte and d_y 8-byte aligned (else AMR_EINVAL).  Waits for the tensor cores are
+   16-byte and d_y 8-byte aligned (else AMR_EINVAL); n = 0 is a no-op (d_x, d_y may be
+   NULL).  Waits for the tensor cores are
    bounded; one that runs out writes AMR_ETIMEOUT to *d_status (may be NULL).
    Asynchronous. */
 amr_status mlp_forward_tc(const void *d_packed, const float *d_x, float *d_y, int64_t n, int32_t *d_status,

@@ -406,8 +406,9 @@ extern "C" amr_status mlp_make_dataset(const double *d_states, int64_t n, double
 
 extern "C" amr_status mlp_forward(const void *d_packed, const float *d_x, float *d_y, int64_t n, amr_stream stream)
 {
-    if (!d_packed || !d_x || !d_y || n < 0) return AMR_EINVAL;
-    if (n == 0) return AMR_OK;
+    if (!d_packed || n < 0) return AMR_EINVAL;
+    if (n == 0) return AMR_OK;                       // no samples: the buffers are not used
+    if (!d_x || !d_y) return AMR_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int64_t warps = (n + 15) / 16;
     const int64_t blocks = (warps + 7) / 8;

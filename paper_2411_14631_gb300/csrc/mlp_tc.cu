@@ -437,9 +437,10 @@ using namespace amr;
 extern "C" amr_status mlp_forward_tc(const void *d_packed, const float *d_x, float *d_y, int64_t n, int32_t *d_status,
                                      amr_stream stream)
 {
-    if (!d_packed || !d_x || !d_y || n < 0) return AMR_EINVAL;
+    if (!d_packed || n < 0) return AMR_EINVAL;
+    if (n == 0) return AMR_OK;                       // no samples: the buffers are not used
+    if (!d_x || !d_y) return AMR_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_x) & 15) || (reinterpret_cast<uintptr_t>(d_y) & 7)) return AMR_EINVAL;
-    if (n == 0) return AMR_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     // at least 116 KB of shared memory: one CTA per SM, which the 512-column TMEM
     // allocation assumes

@@ -81,3 +81,26 @@ def test_tanh_rate_probe(H):
     # of results per SM clock between 4 and 64 on any Blackwell part
     r = H.mlp_tanh_rate()
     assert 4.0 <= r <= 64.0, r
+
+
+def test_forward_tc_empty_and_single_sample(oracle, H):
+    import torch
+    sur = H.Surrogate(theta=_theta(2))
+    # no samples: nothing is launched, the output is not touched
+    x0 = torch.zeros((0, 8), dtype=torch.float32, device="cuda")
+    y0 = torch.zeros((0, 2), dtype=torch.float32, device="cuda")
+    H.mlp_forward_tc(sur.packed, x0, y0)
+    # one sample: a tile of one row, the other 127 rows never written
+    rng = np.random.default_rng(3)
+    x7 = rng.normal(0, 1, (1, 7))
+    x7[:, 6] = 1.4
+    xd = torch.as_tensor(_x8(x7)).cuda()
+    y = torch.full((4, 2), 7.0, dtype=torch.float32, device="cuda")     # one row used, three guards
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    H.mlp_forward_tc(sur.packed, xd, y[:1], status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    yc = y.cpu().numpy()
+    assert np.all(yc[1:] == 7.0)
+    y_o = oracle.mlp_forward(sur.theta.cpu().numpy().astype(np.float64), x7)
+    assert np.abs(yc[:1] - y_o).max() <= 3e-2 * max(np.abs(y_o).max(), 1e-6)

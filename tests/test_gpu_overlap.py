@@ -80,3 +80,15 @@ def test_restrict_complete_arguments(H):
     assert abi.lib().hydro_restrict_complete(None, None, None) == abi.EINVAL
     import ctypes
     assert abi.lib().hydro_restrict_complete(ctypes.byref(g.t), None, None) == abi.EINVAL
+
+
+def test_restrict_complete_is_a_no_op_on_box_batches(H):
+    import torch
+    g = H.Octree.boxes([16, 32], (1,) * 6)
+    assert g.n_inst == 2
+    u = torch.randn((5, g.ncell), dtype=torch.float64, device="cuda")
+    before = u.clone()
+    H.hydro_restrict_complete(g, u)
+    torch.cuda.synchronize()
+    assert torch.equal(u, before)
+

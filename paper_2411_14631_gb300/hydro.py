@@ -148,6 +148,16 @@ class Params:
                                  0.0, limiter, self.status.data_ptr(), self.counters.data_ptr(), col_kernel, col_seg,
                                  int(defer_restriction), 0)
 
+    def with_fields(self, **fields):
+        """A copy of these parameters with some hydro_params fields replaced; it shares the
+        device status word and counters."""
+        q = Params.__new__(Params)
+        q.status, q.counters = self.status, self.counters
+        q.c = abi.HydroParams.from_buffer_copy(self.c)
+        for k, v in fields.items():
+            setattr(q.c, k, v)
+        return q
+
     def read_status(self):
         s = C.c_int32()
         cnt = (C.c_ulonglong * abi.NCOUNTERS)()
@@ -406,10 +416,7 @@ class Simulation:
         self.overlap = bool(overlap) and tree.t.n_inst == 0 and int(tree.t.grid_level) >= 3
         if self.overlap:
             # the same parameters (and device status words), with the restriction deferred
-            self.prm_step = Params.__new__(Params)
-            self.prm_step.status, self.prm_step.counters = prm.status, prm.counters
-            self.prm_step.c = abi.HydroParams.from_buffer_copy(prm.c)
-            self.prm_step.c.defer_restriction = 1
+            self.prm_step = prm.with_fields(defer_restriction=1)
             self._aux = torch.cuda.Stream(device=tree.device)
             self._ev_fork = [torch.cuda.Event(), torch.cuda.Event()]
             self._ev_done = [torch.cuda.Event(), torch.cuda.Event()]

@@ -149,7 +149,7 @@ __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsig
 // depth-2 CTA's shared memory admits one per SM, so it may take every register (no
 // spills); the FP32 depth-1 update (HLLC or exact) fits 64 registers, eight CTAs per SM;
 // the FP64 and surrogate variants keep the compiler's own budget.
-template <int D> constexpr int threads_for() { return D == 1 ? 128 : 512; }
+template <int D> __host__ __device__ constexpr int threads_for() { return D == 1 ? 128 : 512; }
 template <typename R, int D, int RS> constexpr int min_ctas_for()
 {
     return (D == 1 && sizeof(R) == 4 && RS != AMR_RIEMANN_MLP) ? 8 : 1;
@@ -492,6 +492,37 @@ __global__ void __launch_bounds__(threads_for<D>(), (min_ctas_for<R, D, RS>())) 
         __syncthreads();
         if (a.harvest) continue;   // harvesting only: no update (the loop ends with no barrier due)
 
+        // ---- flux register: oct sides whose neighbour slot is a coarse leaf (face fluxes
+        // only, so it may run beside the update)
+        constexpr int NREG = G::OI * G::OI * G::OI * 6;
+        auto reg_task = [&](int w) {
+            const int o = w / 6, f = w % 6, d = f >> 1, side = f & 1;
+            const int ox = 1 + o % G::OI, oy = 1 + (o / G::OI) % G::OI, oz = 1 + o / (G::OI * G::OI);
+            const int32_t e = sm.slot[ox + G::NS * (oy + G::NS * oz)];
+            if (e < 0 || e < tv.reg_base) return;   // base-level octs never face a coarser leaf
+            int nsl[3] = {ox, oy, oz};
+            nsl[d] += side ? 1 : -1;
+            const int32_t en = sm.slot[nsl[0] + G::NS * (nsl[1] + G::NS * nsl[2])];
+            if (en >= 0 || en == OUTSIDE || en == UNNEEDED_SLOT) return;
+            double sum[NV] = {0, 0, 0, 0, 0};
+            for (int c = 0; c < 8; ++c) {
+                const int pc[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+                if (pc[d] != side) continue;
+                const int ii[3] = {2 * ox + pc[0] - 2, 2 * oy + pc[1] - 2, 2 * oz + pc[2] - 2};
+                const int t1 = ii[d == 0 ? 1 : 0], t2 = ii[d == 2 ? 1 : 2];
+                const int r0 = (ii[d] + side) + (G::CI + 1) * (t1 + G::CI * t2);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sum[v] += to_state(sF[d][v][r0]);
+            }
+            const int64_t row = (int64_t(e) - tv.reg_base) * 6 + f;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) a.reg[row * NV + v] = sum[v];
+        };
+        // with depth-1 tiles the update has one cell for half the threads: the other half
+        // writes the register rows meanwhile
+        constexpr bool EARLY_REG = threads_for<D>() >= G::NI + NREG;
+        if (EARLY_REG && a.reg && tid >= G::NI && tid < G::NI + NREG) reg_task(tid - G::NI);
+
         // ---- phase 4: FP64 update of existing cells + fused CFL candidate
         // new states of octs whose father is restricted here, in the (now free) predictor buffer
         double(*sU)[G::NI] = reinterpret_cast<double(*)[G::NI]>(&sm.Q[0][0]);
@@ -569,32 +600,9 @@ __global__ void __launch_bounds__(threads_for<D>(), (min_ctas_for<R, D, RS>())) 
             a.u_new[v * tv.ncell + tv.father[e]] = 0.125 * acc;
         }
 
-        // ---- flux register: oct sides whose neighbour slot is a coarse leaf
-        if (a.reg) {
-            for (int w = tid; w < G::OI * G::OI * G::OI * 6; w += blockDim.x) {
-                const int o = w / 6, f = w % 6, d = f >> 1, side = f & 1;
-                const int ox = 1 + o % G::OI, oy = 1 + (o / G::OI) % G::OI, oz = 1 + o / (G::OI * G::OI);
-                const int32_t e = sm.slot[ox + G::NS * (oy + G::NS * oz)];
-                if (e < 0 || e < tv.reg_base) continue;   // base-level octs never face a coarser leaf
-                int nsl[3] = {ox, oy, oz};
-                nsl[d] += side ? 1 : -1;
-                const int32_t en = sm.slot[nsl[0] + G::NS * (nsl[1] + G::NS * nsl[2])];
-                if (en >= 0 || en == OUTSIDE || en == UNNEEDED_SLOT) continue;
-                double sum[NV] = {0, 0, 0, 0, 0};
-                for (int c = 0; c < 8; ++c) {
-                    const int pc[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
-                    if (pc[d] != side) continue;
-                    const int ii[3] = {2 * ox + pc[0] - 2, 2 * oy + pc[1] - 2, 2 * oz + pc[2] - 2};
-                    const int t1 = ii[d == 0 ? 1 : 0], t2 = ii[d == 2 ? 1 : 2];
-                    const int r0 = (ii[d] + side) + (G::CI + 1) * (t1 + G::CI * t2);
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) sum[v] += to_state(sF[d][v][r0]);
-                }
-                const int64_t row = (int64_t(e) - tv.reg_base) * 6 + f;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) a.reg[row * NV + v] = sum[v];
-            }
-        }
+        // ---- flux register rows (with depth-1 tiles written above, during the update)
+        if (a.reg && !EARLY_REG)
+            for (int w = tid; w < NREG; w += blockDim.x) reg_task(w);
         __syncthreads();
     }
     if (RS == AMR_RIEMANN_MLP && a.counters && (tid & 31) == 0 && (n_acc | n_fb)) {

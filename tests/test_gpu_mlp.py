@@ -127,20 +127,29 @@ def test_adam_step_matches_oracle(oracle, H):
 
 
 def _harvest_sod(H, n_keep=60000):
+    """Face states of 20 Sod steps, the same multiset in the same order on every run: the
+    harvest appends its samples in arrival order, so each step's samples are all kept,
+    sorted (repeated states included) and subsampled with a seeded permutation."""
     import torch
     from paper_2411_14631_gb300.bench_util import cell_centres_of
     tree = H.Octree(W.uniform_tree(5), 5, (1,) * 6)
     prm = H.Params(1.4, cfl=0.8)
     sim = H.Simulation(tree, prm, w0=W.sod_prims(cell_centres_of(tree)))
-    states = torch.empty((n_keep, 6), dtype=torch.float64, device="cuda")
+    cap = 3 * tree.ncell                             # more than the faces of a step
+    states = torch.empty((cap, 6), dtype=torch.float64, device="cuda")
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
     per_step = n_keep // 20
     chunks = []
-    for _ in range(20):
+    for step in range(20):
         count.zero_()
-        H.hydro_harvest_faces(tree, prm, sim.u, sim.dt, states[:per_step], 4, count)
-        k = min(int(count.item()), per_step)
-        chunks.append(states[:k].clone())
+        H.hydro_harvest_faces(tree, prm, sim.u, sim.dt, states, 4, count)
+        k = int(count.item())
+        assert k <= cap
+        uniq, counts = torch.unique(states[:k], dim=0, return_counts=True)
+        rows = torch.repeat_interleave(uniq, counts, dim=0)
+        gen = torch.Generator(device="cpu").manual_seed(step)
+        pick = torch.randperm(rows.shape[0], generator=gen)[:per_step].cuda()
+        chunks.append(rows[pick])
         sim.step()
     return torch.cat(chunks)
 

@@ -368,6 +368,13 @@ __global__ void __launch_bounds__(threads_for<D>(), (min_ctas_for<R, D, RS>())) 
 
     unsigned n_acc = 0, n_fb = 0;   // surrogate: accepted faces, fallbacks (counted by lane 0)
     unsigned n_it = 0, n_solve = 0; // Newton iterations and Newton solves of this thread
+    // The launch has as many CTAs as fit on the GPU at once, each looping over tiles: the
+    // next tile's slot entries and refinement masks are loaded into registers while the
+    // current tile runs (one slot per thread: NSLOT <= threads).
+    static_assert(G::NSLOT <= threads_for<D>(), "one slot per thread");
+    int32_t e_nx = 0;
+    uint8_t rf_nx = 0;
+    bool have_nx = false;
     for (int64_t t = a.t_begin + blockIdx.x; t < a.t_end; t += gridDim.x) {
         // ---- level of this tile and its geometry
         const int32_t root = a.tile_root[t];
@@ -398,13 +405,25 @@ __global__ void __launch_bounds__(threads_for<D>(), (min_ctas_for<R, D, RS>())) 
         }
         int mine_out = 0;
         const bool finer = !a.tile_inst && l < tv.levelmax;   // only then can a stencil cell be refined
-        for (int s = tid; s < G::NSLOT; s += blockDim.x) {
-            const int32_t e = a.tile_slot[t * G::NSLOT + s];
-            sm.slot[s] = e;
-            sm.ref[s] = (e >= 0 && finer) ? tv.refmask[e] : 0;
-            mine_out |= (e == OUTSIDE);
+        if (tid < G::NSLOT) {
+            int32_t e;
+            uint8_t rf;
+            if (have_nx) {
+                e = e_nx;
+                rf = rf_nx;
+            } else {
+                e = a.tile_slot[t * G::NSLOT + tid];
+                rf = e >= 0 ? tv.refmask[e] : 0;
+            }
+            sm.slot[tid] = e;
+            sm.ref[tid] = (e >= 0 && finer) ? rf : 0;
+            mine_out = (e == OUTSIDE);
         }
         const int any_outside = __syncthreads_or(mine_out);   // barrier: slots visible to all
+        // the next tile's slot entries (their refinement masks after the predictor)
+        const int64_t t_nx = t + gridDim.x;
+        have_nx = t_nx < a.t_end;
+        if (have_nx && tid < G::NSLOT) e_nx = a.tile_slot[t_nx * G::NSLOT + tid];
 
         // ---- phase 1: gather + primitives (c fastest so a warp reads whole octs)
         for (int q = tid; q < G::NC; q += blockDim.x) {
@@ -477,6 +496,8 @@ __global__ void __launch_bounds__(threads_for<D>(), (min_ctas_for<R, D, RS>())) 
                 for (int v = 0; v < NV; ++v) sm.Q[NV + NV * d + v][p] = Dl[d][v];
         }
         __syncthreads();
+
+        if (have_nx && tid < G::NSLOT) rf_nx = e_nx >= 0 ? tv.refmask[e_nx] : 0;
 
         // ---- phase 3: Riemann problem at every face touching an updated cell
         if constexpr (RS == AMR_RIEMANN_MLP) {
@@ -625,7 +646,15 @@ static amr_status launch(const GArgs &a, int64_t ntile, cudaStream_t st)
     const size_t bytes = sizeof(Smem<R, D, RS>);
     auto kern = k_godunov<R, D, RS>;
     AMR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
-    const int64_t grid = ntile < 1048576 ? ntile : 1048576;
+    // as many CTAs as are resident at once (each loops over tiles and prefetches the next
+    // tile's slot table)
+    int dev = 0, nsm = 152, per_sm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads_for<D>(), bytes) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int64_t resident = int64_t(per_sm) * nsm;
+    const int64_t grid = ntile < resident ? ntile : resident;
     kern<<<unsigned(grid), threads_for<D>(), bytes, st>>>(a);
     AMR_CUDA_TRY(cudaGetLastError());
     return AMR_OK;

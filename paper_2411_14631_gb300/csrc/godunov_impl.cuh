@@ -136,10 +136,28 @@ __global__ void __launch_bounds__(256) k_ghost(TreeView tv, const double *__rest
     if (g >= g1) return;
     R uc[NV], m[3][NV];
     interp_slopes<R>(tv, u, tv.ghost_cell[g], uc, m);
+    // a father's eight children are 8 consecutive values (32 or 64 bytes from a multiple
+    // of that offset): 16-byte stores when the buffer is 16-byte aligned
+    const bool vec = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
+    for (int v = 0; v < NV; ++v) {
+        R ch[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) out[v * stride + 8 * g + c] = interp_value<R>(uc[v], m, v, c);
+        for (int c = 0; c < 8; ++c) ch[c] = interp_value<R>(uc[v], m, v, c);
+        R *o = out + v * stride + 8 * g;
+        if (vec) {
+            if constexpr (sizeof(R) == 4) {
+                reinterpret_cast<float4 *>(o)[0] = make_float4(ch[0], ch[1], ch[2], ch[3]);
+                reinterpret_cast<float4 *>(o)[1] = make_float4(ch[4], ch[5], ch[6], ch[7]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) reinterpret_cast<double2 *>(o)[k] = make_double2(ch[2 * k], ch[2 * k + 1]);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) o[c] = ch[c];
+        }
+    }
 }
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }

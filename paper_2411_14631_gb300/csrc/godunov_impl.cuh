@@ -2,16 +2,18 @@
 // sibling octs.  A depth-D tile is the 2^D x 2^D x 2^D block of level-l octs below one
 // level-(l-D) oct; its ghosted stencil is (2^D+2)^3 oct slots = (2^(D+1)+4)^3 cells.
 // Phases, all through shared memory:
-//   1 gather the stencil from u_old (FP64 loads; a slot is a level-l oct, a coarse leaf
-//     cell interpolated to its eight children, a clamped outflow ghost, or unused),
-//     convert to primitives in the working precision R;
-//   2 MinMod slopes and the MUSCL-Hancock half-step predictor for every stencil cell
-//     that borders an updated cell;
+//   1 gather the stencil cells that phase 2 reads from u_old (FP64 loads; a slot is a
+//     level-l oct, a coarse leaf cell interpolated to its eight children, a clamped
+//     outflow ghost, or unused; no corner slot is read), convert to primitives in the
+//     working precision R;
+//   2 MinMod slopes and the MUSCL-Hancock half-step predictor for the updated cells and
+//     their face neighbours (the cells the faces read);
 //   3 one Riemann solve per face touching an updated cell;
 //   4 FP64 conservative update of the tile's existing octs, fused CFL candidate for the
 //     next step, and flux-register rows for oct sides facing coarser leaves.
 #pragma once
 #include <cfloat>
+#include <type_traits>
 #include "hydro_math.cuh"
 #include "mlp_warp.cuh"
 #include "godunov_col.cuh"
@@ -32,6 +34,16 @@ template <int D> struct Geo {
     static constexpr int NI = CI * CI * CI;
     static constexpr int NF = (CI + 1) * CI * CI;  // faces per direction
     static constexpr int OI = 1 << D;            // interior oct slots per axis
+    // What the phases read.  The faces need the predicted states of the updated cells and of
+    // their face neighbours (no edge or corner cells of the predicted block): NPN cells.
+    // Those read their face neighbours: the stencil cells at most two cells outside the
+    // updated block in one axis, or one cell outside in two axes.  By slot: every cell of
+    // the interior and face slots (NFULL), the two cells next to the interior of each edge
+    // slot (NEDGE), nothing of the corner slots.
+    static constexpr int NPN = CI * CI * CI + 6 * CI * CI;
+    static constexpr int NFULL = OI * OI * OI + 6 * OI * OI;
+    static constexpr int NEDGE = 12 * OI;
+    static constexpr int NG = 8 * NFULL + 2 * NEDGE;
 };
 
 struct GArgs {
@@ -182,8 +194,13 @@ struct Smem {
     uint8_t ref[G::NSLOT];
     // surrogate staging, per warp: 32 faces x 8 features, then 32 x 2 outputs
     float mlpx[RS == AMR_RIEMANN_MLP ? threads_for<D>() / 32 : 1][RS == AMR_RIEMANN_MLP ? 32 * 10 : 1];
-    double dtmin[32];
+    // the cells the phases read (built once per CTA): interior and face slots, edge-slot
+    // cells (slot << 3 | child), predicted cells
+    uint8_t gfull[G::NFULL];
+    uint16_t gedge[2 * G::NEDGE];
+    std::conditional_t<(G::NP < 256), uint8_t, uint16_t> plist[G::NPN];
 };
+static_assert(Geo<2>::NSLOT <= 256, "slot indices fit a byte");
 
 // left and right states of face r0 of direction DIR (face-normal frame), floored
 template <typename R, int D, int RS, int DIR>
@@ -393,6 +410,47 @@ __global__ void __launch_bounds__(threads_for<D>(), (min_ctas_for<R, D, RS>())) 
     int32_t e_nx = 0;
     uint8_t rf_nx = 0;
     bool have_nx = false;
+    {
+        // the lists of the cells the phases read, compacted in index order by warps 0-2
+        // (visible to all after the first tile's slot barrier)
+        const int lane = tid & 31, w = tid >> 5;
+        const unsigned below = (1u << lane) - 1u;
+        auto bnd = [](int i, int n) { return int(i == 0 || i == n - 1); };
+        int n = 0;
+        if (w == 0) {
+            for (int b = 0; b < G::NSLOT; b += 32) {
+                const int s = b + lane;
+                const bool want = s < G::NSLOT &&
+                                  bnd(s % G::NS, G::NS) + bnd((s / G::NS) % G::NS, G::NS) + bnd(s / (G::NS * G::NS), G::NS) <= 1;
+                const unsigned m = __ballot_sync(0xffffffffu, want);
+                const int k = n + __popc(m & below);
+                if (want && k < G::NFULL) sm.gfull[k] = uint8_t(s);
+                n += __popc(m);
+            }
+        } else if (w == 1) {
+            auto out = [](int i) { return i < 2 ? 2 - i : (i > G::C - 3 ? i - (G::C - 3) : 0); };
+            for (int b = 0; b < 8 * G::NSLOT; b += 32) {
+                const int q = b + lane, sl = q >> 3, c = q & 7;
+                const int sx = sl % G::NS, sy = (sl / G::NS) % G::NS, sz = sl / (G::NS * G::NS);
+                const bool want = q < 8 * G::NSLOT && bnd(sx, G::NS) + bnd(sy, G::NS) + bnd(sz, G::NS) == 2 &&
+                                  out(2 * sx + (c & 1)) + out(2 * sy + ((c >> 1) & 1)) + out(2 * sz + (c >> 2)) == 2;
+                const unsigned m = __ballot_sync(0xffffffffu, want);
+                const int k = n + __popc(m & below);
+                if (want && k < 2 * G::NEDGE) sm.gedge[k] = uint16_t(q);
+                n += __popc(m);
+            }
+        } else if (w == 2) {
+            for (int b = 0; b < G::NP; b += 32) {
+                const int p = b + lane;
+                const bool want = p < G::NP &&
+                                  bnd(p % G::P, G::P) + bnd((p / G::P) % G::P, G::P) + bnd(p / (G::P * G::P), G::P) <= 1;
+                const unsigned m = __ballot_sync(0xffffffffu, want);
+                const int k = n + __popc(m & below);
+                if (want && k < G::NPN) sm.plist[k] = p;
+                n += __popc(m);
+            }
+        }
+    }
     for (int64_t t = a.t_begin + blockIdx.x; t < a.t_end; t += gridDim.x) {
         // ---- level of this tile and its geometry
         const int32_t root = a.tile_root[t];
@@ -443,9 +501,18 @@ __global__ void __launch_bounds__(threads_for<D>(), (min_ctas_for<R, D, RS>())) 
         have_nx = t_nx < a.t_end;
         if (have_nx && tid < G::NSLOT) e_nx = a.tile_slot[t_nx * G::NSLOT + tid];
 
-        // ---- phase 1: gather + primitives (c fastest so a warp reads whole octs)
-        for (int q = tid; q < G::NC; q += blockDim.x) {
-            const int s = q >> 3, c = q & 7;
+        // ---- phase 1: gather + primitives of the listed cells (c fastest so a warp reads
+        // whole octs)
+        for (int kg = tid; kg < G::NG; kg += blockDim.x) {
+            int s, c;
+            if (kg < 8 * G::NFULL) {
+                s = sm.gfull[kg >> 3];
+                c = kg & 7;
+            } else {
+                const int q = sm.gedge[kg - 8 * G::NFULL];
+                s = q >> 3;
+                c = q & 7;
+            }
             const int sx = s % G::NS, sy = (s / G::NS) % G::NS, sz = s / (G::NS * G::NS);
             const int i = 2 * sx + (c & 1), j = 2 * sy + ((c >> 1) & 1), k = 2 * sz + ((c >> 2) & 1);
             const int si = i + G::C * (j + G::C * k);
@@ -489,10 +556,11 @@ __global__ void __launch_bounds__(threads_for<D>(), (min_ctas_for<R, D, RS>())) 
             __syncthreads();
         }
 
-        // ---- phase 2: slopes + predictor on stencil cells 1..C-2
+        // ---- phase 2: slopes + predictor on the listed cells of stencil 1..C-2
         const R lamR = to_work<R>(lam);
         const R hl = R(0.5) * lamR;
-        for (int p = tid; p < G::NP; p += blockDim.x) {
+        for (int kp = tid; kp < G::NPN; kp += blockDim.x) {
+            const int p = sm.plist[kp];
             const int i = 1 + p % G::P, j = 1 + (p / G::P) % G::P, k = 1 + p / (G::P * G::P);
             const int si = i + G::C * (j + G::C * k);
             const int st[3] = {1, G::C, G::C * G::C};
@@ -661,6 +729,11 @@ template <typename R, int D, int RS>
 static amr_status launch(const GArgs &a, int64_t ntile, cudaStream_t st)
 {
     if (ntile <= 0) return AMR_OK;
+    // 227 KB per CTA at most; the FP32 depth-1 update keeps eight CTAs in an SM's 228 KB
+    // (each with its 1 KB reserved by the system)
+    static_assert(sizeof(Smem<R, D, RS>) <= 227 * 1024, "tile shared memory");
+    static_assert(min_ctas_for<R, D, RS>() == 1 || (sizeof(Smem<R, D, RS>) + 1024) * 8 <= 228 * 1024,
+                  "eight depth-1 CTAs per SM");
     const size_t bytes = sizeof(Smem<R, D, RS>);
     auto kern = k_godunov<R, D, RS>;
     AMR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));

@@ -352,7 +352,8 @@ __global__ void k_tile_counts(BuildView b, const int32_t *__restrict__ pos, int 
 }
 
 // Stencil slots of each tile: a depth-D tile covers 2^D x 2^D x 2^D level-l octs and
-// its stencil (2^D + 2)^3 oct positions, one layer of octs (two cells) around it.
+// its stencil (2^D + 2)^3 oct positions, one layer of octs (two cells) around it; the
+// eight corner positions are marked unneeded.
 __global__ void k_tile_slots(BuildView b, int depth, int64_t ntile, const int32_t *__restrict__ root,
                              const int32_t *__restrict__ son, int32_t *slot)
 {
@@ -364,6 +365,12 @@ __global__ void k_tile_slots(BuildView b, int depth, int64_t ntile, const int32_
     const int32_t r = root[t];
     const int l = b.lvl[r] + depth;
     const int sx = s % ns, sy = (s / ns) % ns, sz = s / (ns * ns);
+    // the eight corner slots: the update reads none of their cells (its faces need the
+    // predicted states of face neighbours only), so they get no ghost father either
+    if (int(sx == 0 || sx == ns - 1) + int(sy == 0 || sy == ns - 1) + int(sz == 0 || sz == ns - 1) == 3) {
+        slot[gi] = UNNEEDED;
+        return;
+    }
     // level-l oct coordinates == level-(l-1) father cell coordinates
     int64_t P[3] = {int64_t(b.ix[r]) * (1 << depth) - 1 + sx, int64_t(b.iy[r]) * (1 << depth) - 1 + sy,
                     int64_t(b.iz[r]) * (1 << depth) - 1 + sz};

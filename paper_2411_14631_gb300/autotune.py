@@ -9,8 +9,8 @@ every candidate gives bitwise identical states and time steps (tested):
 The column candidates are timed first (tile depth at its default), then the tile depths
 with the fastest column shape; a mesh with no tile levels skips the second round.  Each
 candidate runs a few whole steps on the actual mesh, timed with CUDA events; the winner
-is cached per (mesh, precision, Riemann solver, GPU name) in a JSON file (default
-``~/.cache/amrhydro/tune.json``, or ``$AMRHYDRO_TUNE_CACHE``)."""
+is cached per (mesh, precision, Riemann solver, GPU name, kernel source version) in a
+JSON file (default ``~/.cache/amrhydro/tune.json``, or ``$AMRHYDRO_TUNE_CACHE``)."""
 import hashlib
 import json
 import os
@@ -19,6 +19,7 @@ import numpy as np
 import torch
 
 from . import abi
+from . import build
 from . import hydro as H
 
 CACHE_VERSION = 3
@@ -35,7 +36,9 @@ def mesh_key(tree, precision, riemann):
     h.update(np.asarray(tree.t.bc[:]).tobytes())
     h.update(np.asarray([int(tree.t.n_inst), int(tree.t.grid_level), int(tree.t.col_work)]).tobytes())
     gpu = torch.cuda.get_device_name(tree.device)
-    return "v%d|%s|p%d|r%d|%s" % (CACHE_VERSION, h.hexdigest()[:16], precision, riemann, gpu)
+    # a winner timed on other kernel code is timed again
+    return "v%d|%s|p%d|r%d|%s|%s" % (CACHE_VERSION, h.hexdigest()[:16], precision, riemann, gpu,
+                                     build.library_hash())
 
 
 def _name(c):

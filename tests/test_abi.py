@@ -119,3 +119,25 @@ def test_poisson_entry_points_validate_on_host(built, tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert got == [C.sizeof(abi.PpcgParams), C.sizeof(abi.PpcgInfo), abi.PpcgParams.seg.offset,
                    abi.PpcgInfo.eps.offset]
+
+
+def test_every_struct_field_offset_matches_c(tmp_path):
+    """Each field of the ctypes mirrors sits at the offset the C compiler gives it (a swap
+    of two equal-sized fields keeps the struct size and would pass a size check)."""
+    from paper_2411_14631_gb300 import abi
+    structs = {"amr_tree": abi.AmrTree, "hydro_params": abi.HydroParams, "amr_geom": abi.AmrGeom,
+               "ppcg_params": abi.PpcgParams, "ppcg_info": abi.PpcgInfo}
+    lines = []
+    for cname, S in structs.items():
+        for f in S._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f[0], cname, f[0]))
+    src = tmp_path / "off.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "amrhydro.h"\n#include "ppcg.h"\n'
+                   'int main(){%s}\n' % "\n".join(lines))
+    exe = tmp_path / "off"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for cname, S in structs.items():
+        for f in S._fields_:
+            assert int(got["%s.%s" % (cname, f[0])]) == getattr(S, f[0]).offset, (cname, f[0])

@@ -151,6 +151,10 @@ class Params:
     def with_fields(self, **fields):
         """A copy of these parameters with some hydro_params fields replaced; it shares the
         device status word and counters."""
+        known = {f[0] for f in abi.HydroParams._fields_}
+        unknown = sorted(set(fields) - known)
+        if unknown:
+            raise TypeError("hydro_params has no field %s" % ", ".join(unknown))
         q = Params.__new__(Params)
         q.status, q.counters = self.status, self.counters
         q.c = abi.HydroParams.from_buffer_copy(self.c)

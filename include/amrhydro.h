@@ -139,7 +139,9 @@ typedef struct {
     int32_t *tile_root[2];                  /* per tile: root oct (level l-d-1); batch mode: corner oct */
     int32_t *tile_slot[2];                  /* per tile: (2^(d+1)+2)^3 stencil slots: an oct (>= 0), a
                                                ghost father -(1+g), INT32_MIN beyond an outflow face,
-                                               or INT32_MIN+1 (not needed) */
+                                               or INT32_MIN+1 (not needed: no updated oct reaches it;
+                                               always so for the eight corner slots of a tree-mode
+                                               tile, whose cells no face reads) */
     /* batch mode (n_inst > 0): octs of box i are [inst_oct_off[i], inst_oct_off[i+1]) in
        lexicographic (ix fastest) order, lvl[oct] holds the box index, no refinement; the
        time step is per box: d_dt and d_dt_next of the hydro calls are arrays [n_inst]. */

@@ -1,5 +1,5 @@
-// godunov_fine (Table 1 of arXiv 2411.14631) on GB300: one CTA updates one tile of
-// sibling octs.  A depth-D tile is the 2^D x 2^D x 2^D block of level-l octs below one
+// godunov_fine (Table 1 of arXiv 2411.14631) on GB300: a CTA updates one tile of sibling
+// octs at a time, looping over tiles.  A depth-D tile is the 2^D x 2^D x 2^D block of level-l octs below one
 // level-(l-D) oct; its ghosted stencil is (2^D+2)^3 oct slots = (2^(D+1)+4)^3 cells.
 // Phases, all through shared memory:
 //   1 gather the stencil cells that phase 2 reads from u_old (FP64 loads; a slot is a

@@ -245,7 +245,8 @@ amr_status reflux_level(const amr_tree *tree, int level, const hydro_params *par
                         const double *d_flux_reg, double *d_u_new, const double *d_dt,
                         double *d_dt_next, amr_stream stream);
 
-/* One whole step: resets *d_dt_next (if not NULL) to a large value, then godunov on
+/* One whole step: checks its arguments (AMR_EINVAL as hydro_godunov_level, before
+   anything is written), resets *d_dt_next (if not NULL) to a large value, then godunov on
    every level (one launch), then reflux + restriction from the finest level up.
    Equivalent to the calls above in that order (the same bits): below the deepest
    complete level minus one, where every cell is refined and the step is a pure

@@ -418,9 +418,9 @@ extern "C" amr_status hydro_courant(const amr_tree *t, const hydro_params *p, co
     return AMR_OK;
 }
 
-extern "C" amr_status hydro_godunov_level(const amr_tree *t, int level, const hydro_params *p, const double *d_u_old,
-                                          double *d_u_new, double *d_flux_reg, const double *d_dt, double *d_dt_next,
-                                          amr_stream stream)
+// the argument checks of the update (also made by hydro_step before it writes anything)
+static amr_status godunov_args(const amr_tree *t, int level, const hydro_params *p, const double *d_u_old,
+                               const double *d_u_new, const double *d_flux_reg, const double *d_dt)
 {
     if (check(t, p) != AMR_OK || !d_u_old || !d_u_new || !d_dt) return AMR_EINVAL;
     if ((p->riemann == AMR_RIEMANN_MLP || p->riemann == AMR_RIEMANN_MLP_SEEDED) &&
@@ -428,6 +428,14 @@ extern "C" amr_status hydro_godunov_level(const amr_tree *t, int level, const hy
         return AMR_EINVAL;
     if (level != -1 && (level < t->levelmin || level > t->levelmax)) return AMR_EINVAL;
     if (t->levelmax > t->levelmin && !d_flux_reg) return AMR_EINVAL;
+    return AMR_OK;
+}
+
+extern "C" amr_status hydro_godunov_level(const amr_tree *t, int level, const hydro_params *p, const double *d_u_old,
+                                          double *d_u_new, double *d_flux_reg, const double *d_dt, double *d_dt_next,
+                                          amr_stream stream)
+{
+    if (godunov_args(t, level, p, d_u_old, d_u_new, d_flux_reg, d_dt) != AMR_OK) return AMR_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (p->precision == AMR_PREC_FP32)
         return godunov_dispatch_fp32(t, level, p, d_u_old, d_u_new, d_flux_reg, d_dt, d_dt_next, st);
@@ -526,8 +534,9 @@ extern "C" amr_status hydro_restrict_complete(const amr_tree *t, double *d_u, am
 extern "C" amr_status hydro_step(const amr_tree *t, const hydro_params *p, const double *d_u_old, double *d_u_new,
                                  double *d_flux_reg, const double *d_dt, double *d_dt_next, amr_stream stream)
 {
+    if (godunov_args(t, -1, p, d_u_old, d_u_new, d_flux_reg, d_dt) != AMR_OK) return AMR_EINVAL;
     if (d_dt_next)
-        AMR_CUDA_TRY(cudaMemsetAsync(d_dt_next, 0x7F, sizeof(double) * size_t(t && t->n_inst > 0 ? t->n_inst : 1),
+        AMR_CUDA_TRY(cudaMemsetAsync(d_dt_next, 0x7F, sizeof(double) * size_t(t->n_inst > 0 ? t->n_inst : 1),
                                      reinterpret_cast<cudaStream_t>(stream)));
     amr_status r = hydro_godunov_level(t, -1, p, d_u_old, d_u_new, d_flux_reg, d_dt, d_dt_next, stream);
     if (r != AMR_OK) return r;

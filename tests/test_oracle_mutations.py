@@ -1,0 +1,68 @@
+"""Planted mistakes: each is a plausible slip in the oracle's scheme (a dropped term, a
+wrong sign or index, a wrong factor), planted into a scratch copy of the oracle's C
+source, which is compiled and loaded in place of the real one for the test; the pin
+named beside it must then fail.  The real oracle passes every one of these pins."""
+import os
+import shutil
+
+import numpy as np
+import pytest
+
+import test_oracle_hydro as H
+import test_oracle_truncation as T
+
+# (file, exact text, replacement): the predictor and face states of hydro.c
+PREDICTOR = {
+    "density_divergence_dropped": (
+        "hydro.c",
+        "Wt[0] = r - h * (u * D[0][0] + r * D[0][1] + v * D[1][0] + r * D[1][2] + w * D[2][0] + r * D[2][3]);",
+        "Wt[0] = r - h * (u * D[0][0] + v * D[1][0] + w * D[2][0]);"),
+    "density_advection_dropped_x": ("hydro.c", "Wt[0] = r - h * (u * D[0][0] + ", "Wt[0] = r - h * ("),
+    "velocity_advection_dropped_x": ("hydro.c", "Wt[1] = u - h * (u * D[0][1] + ", "Wt[1] = u - h * ("),
+    "pressure_gradient_dropped_x": ("hydro.c", "+ w * D[2][1] + D[0][4] / r);", "+ w * D[2][1]);"),
+    "pressure_divergence_dropped": ("hydro.c", " + gamma * p * (D[0][1] + D[1][2] + D[2][3]));", ");"),
+    "predictor_full_step": ("hydro.c", "double h = 0.5 * lam;", "double h = lam;"),
+    "face_states_swapped": ("hydro.c", "side ? Wt[v] + 0.5 * D[d][v] : Wt[v] - 0.5 * D[d][v];",
+                            "side ? Wt[v] - 0.5 * D[d][v] : Wt[v] + 0.5 * D[d][v];"),
+}
+OTHER = {
+    "interpolation_sign": (("hydro.c", "r = r + (pos[d] ? 0.25 * m : -0.25 * m);",
+                            "r = r + (pos[d] ? -0.25 * m : 0.25 * m);"),
+                           lambda O: H.test_ghost_interpolation_mean_and_linear(O)),
+    "reflux_sign": (("hydro.c", "side ? u_new[(int64_t)v * ncell + C] - lam * corr",
+                     "side ? u_new[(int64_t)v * ncell + C] + lam * corr"),
+                    lambda O: H.test_conservation_periodic(O, True)),
+}
+
+
+@pytest.fixture
+def planted(oracle, tmp_path, monkeypatch):
+    """Returns a function that plants one mistake and loads the mutated oracle."""
+    def plant(fname, old, new):
+        for s in oracle._SRC + ["oracle.h"]:
+            shutil.copy(os.path.join(oracle._HERE, s), tmp_path)
+        path = os.path.join(tmp_path, fname)
+        src = open(path).read()
+        assert src.count(old) == 1, "the planted text must match exactly once"
+        open(path, "w").write(src.replace(old, new))
+        monkeypatch.setattr(oracle, "_HERE", str(tmp_path))
+        monkeypatch.setattr(oracle, "_LIB_PATH", os.path.join(tmp_path, "liboracle.so"))
+        monkeypatch.setattr(oracle, "_lib", None)
+        return oracle
+    return plant
+
+
+@pytest.mark.parametrize("name", sorted(PREDICTOR))
+def test_predictor_mistakes_fail_the_exact_solution_pin(planted, name):
+    O = planted(*PREDICTOR[name])
+    e5, e6 = T.octree_errors(O, 5), T.octree_errors(O, 6)
+    order = np.log2(e5 / e6)
+    assert not np.all(order > 2.8), (name, order)
+
+
+@pytest.mark.parametrize("name", sorted(OTHER))
+def test_other_mistakes_fail_their_pin(planted, name):
+    mutation, pin = OTHER[name]
+    O = planted(*mutation)
+    with pytest.raises(AssertionError):
+        pin(O)

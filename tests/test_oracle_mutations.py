@@ -1,5 +1,5 @@
-"""Planted mistakes: each is a plausible slip in the oracle's scheme (a dropped term, a
-wrong sign or index, a wrong factor), planted into a scratch copy of the oracle's C
+"""Planted mistakes: each is a plausible slip in the oracle's scheme or its sub-cycling
+(a dropped term, a wrong sign or index, a wrong factor, a missing step), planted into a scratch copy of the oracle's C
 source, which is compiled and loaded in place of the real one for the test; the pin
 named beside it must then fail.  The real oracle passes every one of these pins."""
 import os
@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import test_oracle_hydro as H
+import test_oracle_subcycle as S
 import test_oracle_truncation as T
 
 # (file, exact text, replacement): the predictor and face states of hydro.c
@@ -32,6 +33,28 @@ OTHER = {
     "reflux_sign": (("hydro.c", "side ? u_new[(int64_t)v * ncell + C] - lam * corr",
                      "side ? u_new[(int64_t)v * ncell + C] + lam * corr"),
                     lambda O: H.test_conservation_periodic(O, True)),
+    # level sub-cycling (subcycle.c)
+    "subcycle_no_time_interpolation": (("subcycle.c", "U[i] = 0.5 * (U[i] + N[i]);", "U[i] = U[i];"),
+                                       lambda O: S.test_wave_through_refinement_bands(O)),
+    "subcycle_ghosts_at_the_new_time": (("subcycle.c", "U[i] = 0.5 * (U[i] + N[i]);", "U[i] = N[i];"),
+                                        lambda O: S.test_wave_through_refinement_bands(O)),
+    "subcycle_fine_step_not_halved": (("subcycle.c",
+                                       "x.dt[l] = l >= t->levelmin ? ldexp(dtb, -(l - t->levelmin)) : dtb;",
+                                       "x.dt[l] = dtb;"),
+                                      lambda O: S.test_wave_through_refinement_bands(O)),
+    "subcycle_first_fine_step_not_corrected": (("subcycle.c",
+                                                "        or_reflux_restrict(t, x->p, c, x->reg, x->U, x->dt[c + 1]);\n",
+                                                ""),
+                                               lambda O: S.test_wave_through_refinement_bands(O)),
+    "subcycle_reflux_with_the_coarse_step": (("subcycle.c",
+                                              "        advance(x, c + 1);\n"
+                                              "        or_reflux_restrict(t, x->p, c, x->reg, x->N, x->dt[c + 1]);\n    }",
+                                              "        advance(x, c + 1);\n"
+                                              "        or_reflux_restrict(t, x->p, c, x->reg, x->N, x->dt[c]);\n    }"),
+                                             lambda O: S.test_conservation(O)),
+    "subcycle_courant_not_scaled_by_level": (("subcycle.c", "double r = ldexp(dx / sig, l - t->levelmin);",
+                                              "double r = dx / sig;"),
+                                             lambda O: S.test_time_step_closed_form(O)),
 }
 
 

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import test_oracle_hydro as H
+import test_oracle_riemann as R
 import test_oracle_subcycle as S
 import test_oracle_truncation as T
 
@@ -33,6 +34,19 @@ OTHER = {
     "reflux_sign": (("hydro.c", "side ? u_new[(int64_t)v * ncell + C] - lam * corr",
                      "side ? u_new[(int64_t)v * ncell + C] + lam * corr"),
                     lambda O: H.test_conservation_periodic(O, True)),
+    # HLLC (riemann.c): each caught by the reflection symmetry that maps a branch onto its partner
+    "hllc_left_speed_from_the_wrong_wave": (("riemann.c", "double SL = fmin(uL - cL, uR - cR);",
+                                             "double SL = fmin(uL - cL, uR + cR);"),
+                                            lambda O: R.test_hllc_mirror_symmetry(O)),
+    "hllc_right_star_with_the_left_density": (("riemann.c", "double f = rR * (SR - uR) / (SR - Sstar);",
+                                               "double f = rL * (SR - uR) / (SR - Sstar);"),
+                                              lambda O: R.test_hllc_mirror_symmetry(O)),
+    "hllc_right_star_with_the_left_speed": (("riemann.c",
+                                             "for (int v = 0; v < 5; v++) F[v] = FR[v] + SR * (Us[v] - UR[v]);",
+                                             "for (int v = 0; v < 5; v++) F[v] = FR[v] + SL * (Us[v] - UR[v]);"),
+                                            lambda O: R.test_hllc_mirror_symmetry(O)),
+    "hllc_contact_speed_sign": (("riemann.c", "double Sstar = (pR - pL + rL", "double Sstar = (pL - pR + rL"),
+                                lambda O: R.test_hllc_close_to_exact_for_weak_waves(O)),
     # level sub-cycling (subcycle.c)
     "subcycle_no_time_interpolation": (("subcycle.c", "U[i] = 0.5 * (U[i] + N[i]);", "U[i] = U[i];"),
                                        lambda O: S.test_wave_through_refinement_bands(O)),

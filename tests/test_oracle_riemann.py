@@ -179,3 +179,27 @@ def test_exact_flux_falls_back_on_vacuum(oracle):
     WL = np.array([1.0, -10.0, 0, 0, 0.4]); WR = np.array([1.0, 10.0, 0, 0, 0.4])
     F, st = oracle.riemann_flux(WL, WR, prm)
     assert st == oracle.ENONPHYSICAL and np.array_equal(F, oracle.hllc(WL, WR, G))
+
+
+def _mirror(W):
+    return np.array([W[0], -W[1], W[2], W[3], W[4]])
+
+
+def test_hllc_mirror_symmetry(oracle):
+    """Reflecting the problem (x -> -x: the states swap sides and the normal velocity
+    changes sign) reflects the flux: mass, transverse-momentum and energy fluxes change
+    sign, the normal-momentum flux does not.  The reflection maps every branch of HLLC
+    onto its partner (left star <-> right star, left <-> right supersonic), so each
+    branch is checked against the other."""
+    rng = np.random.default_rng(6)
+    branches = set()
+    for _ in range(400):
+        WL = np.array([rng.uniform(0.1, 5), rng.normal(0, 3), *rng.normal(0, 1, 2), rng.uniform(0.1, 5)])
+        WR = np.array([rng.uniform(0.1, 5), rng.normal(0, 3), *rng.normal(0, 1, 2), rng.uniform(0.1, 5)])
+        F = oracle.hllc(WL, WR, G)
+        Fm = oracle.hllc(_mirror(WR), _mirror(WL), G)
+        assert np.allclose(Fm, F * np.array([-1, 1, -1, -1, -1]), rtol=1e-12, atol=1e-12), (WL, WR)
+        cL, cR = np.sqrt(G * WL[4] / WL[0]), np.sqrt(G * WR[4] / WR[0])
+        SL, SR = min(WL[1] - cL, WR[1] - cR), max(WL[1] + cL, WR[1] + cR)
+        branches.add("L" if SL >= 0 else "R" if SR <= 0 else "star")
+    assert branches == {"L", "R", "star"}

@@ -59,6 +59,25 @@ def test_uniform_flow_across_levels(oracle):
         assert np.max(np.abs(un[v, leaf] - u[v, leaf])) <= 8e-16 * 4 * scale
 
 
+def test_refined_cells_hold_the_mean_of_their_children(oracle):
+    """After a step every refined cell holds the volume average of its eight children
+    (the conservative restriction of the AMR scheme, Teyssier 2002), level by level, so
+    the coarse value is the average of the finest data below it.  Leaf-only checks
+    cannot see this: a coarse leaf next to a refined cell reads the refined cell's value
+    only through a MinMod slope, which a uniform flow keeps at zero."""
+    lx = W.random_tree(3, 2, seed=13, p_refine=0.35, periodic=True)
+    t, prm, u, _ = _setup(oracle, lx, 3, PER, lambda x: _smooth_random(x, 5), 5 / 3, cfl=0.5)
+    for _ in range(2):
+        u, dt, st = t.step(u, prm)
+        assert st == 0
+    refined = np.nonzero(t.son >= 0)[0]
+    assert len(refined) > 0
+    for cell in refined:
+        s = t.son[cell]
+        kids = u[:, 8 * s:8 * s + 8]
+        assert np.allclose(u[:, cell], kids.mean(axis=1), rtol=1e-14, atol=1e-15), cell
+
+
 @pytest.mark.parametrize("amr", [False, True])
 def test_conservation_periodic(oracle, amr):
     if amr:

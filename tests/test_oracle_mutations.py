@@ -34,6 +34,13 @@ OTHER = {
     "reflux_sign": (("hydro.c", "side ? u_new[(int64_t)v * ncell + C] - lam * corr",
                      "side ? u_new[(int64_t)v * ncell + C] + lam * corr"),
                     lambda O: H.test_conservation_periodic(O, True)),
+    "restriction_factor": (("hydro.c", "u_new[(int64_t)v * ncell + o * 8 + c] = 0.125 * sum;",
+                            "u_new[(int64_t)v * ncell + o * 8 + c] = 0.25 * sum;"),
+                           lambda O: H.test_refined_cells_hold_the_mean_of_their_children(O)),
+    "restriction_coarse_level_first": (("hydro.c",
+                                        "for (int l = t->levelmax - 1; l >= 1; l--) or_reflux_restrict(t, p, l, reg, u_new, dt);",
+                                        "for (int l = 1; l <= t->levelmax - 1; l++) or_reflux_restrict(t, p, l, reg, u_new, dt);"),
+                                       lambda O: H.test_refined_cells_hold_the_mean_of_their_children(O)),
     # HLLC (riemann.c): each caught by the reflection symmetry that maps a branch onto its partner
     "hllc_left_speed_from_the_wrong_wave": (("riemann.c", "double SL = fmin(uL - cL, uR - cR);",
                                              "double SL = fmin(uL - cL, uR + cR);"),

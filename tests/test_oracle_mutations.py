@@ -9,7 +9,10 @@ import numpy as np
 import pytest
 
 import test_oracle_hydro as H
+import test_oracle_mlp as M
+import test_oracle_poisson as P
 import test_oracle_riemann as R
+import test_oracle_tree as TR
 import test_oracle_subcycle as S
 import test_oracle_truncation as T
 
@@ -54,6 +57,26 @@ OTHER = {
                                             lambda O: R.test_hllc_mirror_symmetry(O)),
     "hllc_contact_speed_sign": (("riemann.c", "double Sstar = (pR - pL + rL", "double Sstar = (pL - pR + rL"),
                                 lambda O: R.test_hllc_close_to_exact_for_weak_waves(O)),
+    # octree and Hilbert key (tree.c)
+    "hilbert_gray_code_order": (("tree.c", "    X[1] ^= X[0];\n    X[2] ^= X[1];", "    X[2] ^= X[1];\n    X[1] ^= X[0];"),
+                                lambda O: TR.test_hilbert_bijection_and_adjacency(O, 3)),
+    "octree_child_bits_swapped": (("tree.c", "return o * 8 + (X & 1) + 2 * (Y & 1) + 4 * (Z & 1);",
+                                   "return o * 8 + (X & 1) + 4 * (Y & 1) + 2 * (Z & 1);"),
+                                  lambda O: TR.test_tables_match_brute_force(O, 0)),
+    # surrogate network and Adam (mlp.c)
+    "silu_derivative": (("mlp.c", "gz[j] = g[j] * sg * (1.0 + z[L][j] * (1.0 - sg));",
+                         "gz[j] = g[j] * sg * (1.0 + z[L][j] * sg);"),
+                        lambda O: M.test_backward_matches_finite_differences(O)),
+    "adam_without_bias_correction": (("mlp.c", "double mh = m[i] / c1, vh = v[i] / c2;", "double mh = m[i], vh = v[i];"),
+                                     lambda O: M.test_adam_first_step(O)),
+    # Poisson solvers (poisson.c)
+    "preconditioner_centre_weight": (("poisson.c",
+                                      "u[c] = (13.0 / 12.0) * r[c] + nb_sum(r, nx, ny, nz, i, j, k) / 6.0;",
+                                      "u[c] = r[c] + nb_sum(r, nx, ny, nz, i, j, k) / 6.0;"),
+                                     lambda O: P.test_preconditioner_is_incomplete_kkt(O)),
+    "ppcg_step_length_recurrence": (("poisson.c", "alpha = gamma / (delta - beta * gamma / alpha_old);",
+                                     "alpha = gamma / (delta - beta * gamma * alpha_old);"),
+                                    lambda O: P.test_iterates_match_scipy_cg(O, 0)),
     # level sub-cycling (subcycle.c)
     "subcycle_no_time_interpolation": (("subcycle.c", "U[i] = 0.5 * (U[i] + N[i]);", "U[i] = U[i];"),
                                        lambda O: S.test_wave_through_refinement_bands(O)),

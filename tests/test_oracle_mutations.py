@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import test_oracle_hydro as H
+import test_oracle_refine as RF
 import test_oracle_mlp as M
 import test_oracle_poisson as P
 import test_oracle_riemann as R
@@ -57,6 +58,13 @@ OTHER = {
                                             lambda O: R.test_hllc_mirror_symmetry(O)),
     "hllc_contact_speed_sign": (("riemann.c", "double Sstar = (pR - pL + rL", "double Sstar = (pL - pR + rL"),
                                 lambda O: R.test_hllc_close_to_exact_for_weak_waves(O)),
+    # the uniform-box path (box.c), checked against the exact solution on its own
+    "box_pressure_divergence_dropped": (("box.c", " + gamma * p * (D[0][1] + D[1][2] + D[2][3]));", ");"),
+                                        lambda O: T.test_box_step_local_error_is_third_order(O)),
+    # refinement (refine.c)
+    "refinement_mass_with_dx_squared": (("refine.c", "flag[cell] = u[cell] * (dx * dx * dx) > mass_thr;",
+                                         "flag[cell] = u[cell] * (dx * dx) > mass_thr;"),
+                                        lambda O: RF.test_new_octs_match_set_construction(O, True, 1)),
     # octree and Hilbert key (tree.c)
     "hilbert_gray_code_order": (("tree.c", "    X[1] ^= X[0];\n    X[2] ^= X[1];", "    X[2] ^= X[1];\n    X[1] ^= X[0];"),
                                 lambda O: TR.test_hilbert_bijection_and_adjacency(O, 3)),

@@ -159,6 +159,22 @@ def test_courant_closed_form(oracle):
     assert abs(t.courant(u, prm) - 0.7 * (1 / 8) / (0.5 + 1.0 + 0.25 + 3 * c)) <= 1e-15
 
 
+def test_courant_over_leaves_only(oracle):
+    """The time step is the minimum over leaf cells: a refined cell's stored value (here a
+    fast state it would never hold after a restriction) does not enter, and the finest
+    leaves' dx does."""
+    lx = W.random_tree(3, 2, seed=7, p_refine=0.3, periodic=True)
+    t, prm, u, _ = _setup(oracle, lx, 3, PER, lambda x: W.uniform_prims(x, 2.0, (0.5, -1.0, 0.25), 3.0), 1.4,
+                          cfl=0.7)
+    refined = t.son >= 0
+    assert refined.any()
+    fast = t.init_from_prim(W.uniform_prims(np.zeros((t.ncell, 3)), 2.0, (40.0, 0.0, 0.0), 3.0), prm)
+    u[:, refined] = fast[:, refined]
+    c = np.sqrt(1.4 * 3.0 / 2.0)
+    dx_min = np.ldexp(1.0, -int(t.levelmax))
+    assert abs(t.courant(u, prm) - 0.7 * dx_min / (0.5 + 1.0 + 0.25 + 3 * c)) <= 1e-15
+
+
 def _two_level_tree():
     levels = {l: W.full_level(l) for l in range(1, 4)}
     x = np.array([3, 4]); xs, ys, zs = np.meshgrid(x, x, x, indexing="ij")

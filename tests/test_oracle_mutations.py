@@ -45,6 +45,11 @@ OTHER = {
                                         "for (int l = t->levelmax - 1; l >= 1; l--) or_reflux_restrict(t, p, l, reg, u_new, dt);",
                                         "for (int l = 1; l <= t->levelmax - 1; l++) or_reflux_restrict(t, p, l, reg, u_new, dt);"),
                                        lambda O: H.test_refined_cells_hold_the_mean_of_their_children(O)),
+    "courant_over_refined_cells_too": (("hydro.c",
+                                        "            if (t->son[cid] >= 0) continue;\n            double U[NV], W[NV];\n"
+                                        "            load(u, ncell, cid, U);",
+                                        "            double U[NV], W[NV];\n            load(u, ncell, cid, U);"),
+                                       lambda O: H.test_courant_over_leaves_only(O)),
     # HLLC (riemann.c): each caught by the reflection symmetry that maps a branch onto its partner
     "hllc_left_speed_from_the_wrong_wave": (("riemann.c", "double SL = fmin(uL - cL, uR - cR);",
                                              "double SL = fmin(uL - cL, uR + cR);"),

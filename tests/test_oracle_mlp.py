@@ -77,3 +77,17 @@ def test_features_invariant_under_scaling(oracle):
         ps2, us2, _, _ = oracle.exact_star(WL2, WR2, g)
         assert abs(np.log(ps1 / r1[0]) - np.log(ps2 / r2[0])) <= 1e-10
         assert abs((us1 - r1[1]) / r1[2] - (us2 - r2[1]) / r2[2]) <= 1e-10
+
+
+def test_features_worked_examples(oracle):
+    """The normalisation written out by hand for two problems: rho_ref = rho_L,
+    p_ref = max(p_L, p_R), c_ref = sqrt(p_ref / rho_ref), u_bar = (u_L + u_R) / 2."""
+    # Sod's states: rho_ref = 1, p_ref = 1, c_ref = 1, u_bar = 0
+    x, ref = oracle.mlp_features(np.array([1.0, 0, 0, 0, 1.0]), np.array([0.125, 0, 0, 0, 0.1]), 1.4)
+    assert np.allclose(x, [0, 0, 0, np.log(0.125), 0, np.log(0.1), 1.4], rtol=0, atol=1e-15)
+    assert np.allclose(ref, [1.0, 0.0, 1.0], rtol=0, atol=1e-15)
+    # a collision with the higher pressure on the right: rho_ref = 4, p_ref = 4,
+    # c_ref = 1, u_bar = 0.5
+    x, ref = oracle.mlp_features(np.array([4.0, 2.5, 0, 0, 1.0]), np.array([1.0, -1.5, 0, 0, 4.0]), 5 / 3)
+    assert np.allclose(x, [0, 2.0, np.log(0.25), np.log(0.25), -2.0, 0, 5 / 3], rtol=0, atol=1e-15)
+    assert np.allclose(ref, [4.0, 0.5, 1.0], rtol=0, atol=1e-15)

@@ -80,6 +80,11 @@ OTHER = {
     "silu_derivative": (("mlp.c", "gz[j] = g[j] * sg * (1.0 + z[L][j] * (1.0 - sg));",
                          "gz[j] = g[j] * sg * (1.0 + z[L][j] * sg);"),
                         lambda O: M.test_backward_matches_finite_differences(O)),
+    "features_pressure_reference_min": (("mlp.c", "double pref = WL[4] > WR[4] ? WL[4] : WR[4];",
+                                         "double pref = WL[4] < WR[4] ? WL[4] : WR[4];"),
+                                        lambda O: M.test_features_worked_examples(O)),
+    "features_mean_velocity_left_only": (("mlp.c", "double ubar = 0.5 * (WL[1] + WR[1]);", "double ubar = WL[1];"),
+                                         lambda O: M.test_features_worked_examples(O)),
     "adam_without_bias_correction": (("mlp.c", "double mh = m[i] / c1, vh = v[i] / c2;", "double mh = m[i], vh = v[i];"),
                                      lambda O: M.test_adam_first_step(O)),
     # Poisson solvers (poisson.c)
